@@ -1,0 +1,394 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+None of these compares the oracle with itself or with the CUDA path.  Each
+pin targets a different plausible mistake: a dropped r^-6 term, a wrong
+sign or factor in the gradient, a transposed or mis-ordered history index in
+the two-loop recursion, a wrong interpolation formula, a broken Philox round,
+an inverted Metropolis or adaptation rule.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_25938_gb300 import inputs
+
+R_MIN = 2.0 ** (1.0 / 6.0)          # pair minimum of Eq. (1) for sigma = 1
+
+
+def rand_cluster(n, seed, side=None, dmin=0.85):
+    """Random cluster with no pair closer than dmin (rejection sampling)."""
+    rng = np.random.default_rng(seed)
+    side = side or (n / 0.3) ** (1 / 3)
+    pts = []
+    while len(pts) < n:
+        p = rng.random(3) * side
+        if all(np.linalg.norm(p - q) >= dmin for q in pts):
+            pts.append(p)
+    return np.array(pts).reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11): published known-answer vectors.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ctr,key,expect", [
+    ([0, 0, 0, 0], [0, 0], [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+    ([0xffffffff] * 4, [0xffffffff] * 2, [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+    ([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [0xa4093822, 0x299f31d0],
+     [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]),
+])
+def test_philox_known_answers(ctr, key, expect):
+    assert O.philox4x32_10(ctr, key).tolist() == expect
+
+
+def test_u01_range_and_exactness():
+    assert O.u01(0, 0) == 0.0
+    assert O.u01(0xffffffff, 0xffffffff) == 1.0 - 2.0 ** -53
+    # 27 bits from the first word, 26 from the second
+    assert O.u01(1 << 5, 0) == 2.0 ** -27
+    assert O.u01(0, 1 << 6) == 2.0 ** -53
+    assert O.u01(31, 63) == 0.0
+
+
+def test_perturbation_uniform_statistics():
+    # x = 0, step = 0.5: delta = u - 1/2 exactly, so u is recovered exactly
+    n = 200_000
+    d = O.perturb(np.zeros(n), 0.5, seed=12345, k=3, s=7, w=11)
+    u = d + 0.5
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 4 * math.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 0.002
+    counts, _ = np.histogram(u, bins=32, range=(0, 1))
+    chi2 = ((counts - n / 32) ** 2 / (n / 32)).sum()
+    assert chi2 < 70          # 31 dof, p ~ 1e-4
+
+
+def test_perturbation_streams_distinct_and_bounded():
+    x = np.linspace(-1, 1, 39)
+    a = O.perturb(x, 0.4, 7, 0, 0, 0)
+    assert np.all(np.abs(a - x) <= 0.4)
+    for args in [(7, 1, 0, 0), (7, 0, 1, 0), (7, 0, 0, 1), (8, 0, 0, 0)]:
+        b = O.perturb(x, 0.4, *args)
+        assert not np.array_equal(a, b)
+    assert np.array_equal(a, O.perturb(x, 0.4, 7, 0, 0, 0))
+
+
+# --------------------------------------------------------------------------
+# Eq. (1): closed forms
+# --------------------------------------------------------------------------
+def test_dimer_closed_form():
+    e, g = O.lj_energy_grad([0, 0, 0, R_MIN, 0, 0])
+    assert abs(e + 1.0) < 1e-15
+    assert np.abs(g).max() < 1e-13
+    e, g = O.lj_energy_grad([0, 0, 0, 1.0, 0, 0])
+    assert e == 0.0
+    # at r = sigma the force is repulsive: dE/dr = 24 (1 - 2) ... = -24 * (2-1)/1 * r
+    assert g[3] == pytest.approx(-24.0) and g[0] == pytest.approx(24.0)
+    for r in (0.9, 1.3, 2.7):
+        e, _ = O.lj_energy_grad([0, 0, 0, 0, 0, r])
+        assert e == pytest.approx(4 * (r ** -12 - r ** -6), rel=1e-14)
+
+
+def test_trimer_and_tetramer_closed_forms():
+    a = R_MIN
+    tri = np.array([[0, 0, 0], [a, 0, 0], [a / 2, a * math.sqrt(3) / 2, 0]])
+    e, g = O.lj_energy_grad(tri)
+    assert e == pytest.approx(-3.0, abs=1e-13)
+    assert np.abs(g).max() < 1e-12
+    tet = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float)
+    tet *= a / np.linalg.norm(tet[0] - tet[1])
+    e, g = O.lj_energy_grad(tet)
+    assert e == pytest.approx(-6.0, abs=1e-13)
+    assert np.abs(g).max() < 1e-12
+
+
+def icosahedron13(radius=1.0):
+    phi = (1 + math.sqrt(5)) / 2
+    v = []
+    for s1 in (-1, 1):
+        for s2 in (-1, 1):
+            v += [(0, s1, s2 * phi), (s1, s2 * phi, 0), (s2 * phi, 0, s1)]
+    v = np.array(v, float)
+    v *= radius / np.linalg.norm(v[0])
+    return np.vstack([np.zeros(3), v])
+
+
+def test_scaled_icosahedron_is_stationary_at_closed_form_scale():
+    """For a fixed shape with unit-scale distances d_ij, E(s) = 4(A s^-12 - B s^-6)
+    with A = sum d^-12, B = sum d^-6, minimised at s^6 = 2A/B with E* = -B^2/A.
+    Under I_h the breathing mode is the only symmetric degree of freedom, so
+    the optimally scaled icosahedron is a stationary point of Eq. (1)."""
+    ico = icosahedron13(1.0)
+    d = np.linalg.norm(ico[:, None] - ico[None], axis=-1)[np.triu_indices(13, 1)]
+    A, B = (d ** -12).sum(), (d ** -6).sum()
+    s_star = (2 * A / B) ** (1 / 6)
+    e, g = O.lj_energy_grad(ico * s_star)
+    assert e == pytest.approx(-B * B / A, rel=1e-13)
+    assert np.abs(g).max() < 1e-11
+    # minimisation from a radially breathed, slightly rotated copy lands on E*
+    x0 = ico * s_star * 1.04
+    x, f, st, it, _ = O.minimize(x0)
+    assert st == O.CONVERGED
+    assert f == pytest.approx(-B * B / A, abs=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Gradient: central finite differences, invariances, scaling law
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,seed", [(5, 1), (13, 2), (38, 3)])
+def test_gradient_central_differences(n, seed):
+    x = rand_cluster(n, seed)
+    _, g = O.lj_energy_grad(x)
+    h = 1e-5
+    fd = np.zeros_like(x)
+    for c in range(x.size):
+        xp = x.copy(); xp[c] += h
+        xm = x.copy(); xm[c] -= h
+        fd[c] = (O.lj_energy_grad(xp)[0] - O.lj_energy_grad(xm)[0]) / (2 * h)
+    scale = max(np.abs(g).max(), 1.0)
+    assert np.abs(fd - g).max() < 1e-6 * scale
+
+
+def test_translation_rotation_permutation_invariance():
+    x = rand_cluster(13, 5).reshape(-1, 3)
+    e0, g0 = O.lj_energy_grad(x)
+    g0 = g0.reshape(-1, 3)
+    # translation: same energy, forces sum to zero
+    e1, _ = O.lj_energy_grad(x + np.array([3.1, -2.2, 0.7]))
+    assert e1 == pytest.approx(e0, rel=1e-13)
+    assert np.abs(g0.sum(0)).max() < 1e-11 * max(1, np.abs(g0).max())
+    # rotation: same energy, zero total torque, gradient rotates
+    q, _ = np.linalg.qr(np.random.default_rng(9).normal(size=(3, 3)))
+    e2, g2 = O.lj_energy_grad(x @ q.T)
+    assert e2 == pytest.approx(e0, rel=1e-12)
+    assert np.allclose(g2.reshape(-1, 3), g0 @ q.T, atol=1e-10)
+    torque = np.cross(x, g0).sum(0)
+    assert np.abs(torque).max() < 1e-10 * max(1, np.abs(g0).max())
+    # permutation: same energy, permuted gradient
+    perm = np.random.default_rng(4).permutation(13)
+    e3, g3 = O.lj_energy_grad(x[perm])
+    assert e3 == pytest.approx(e0, rel=1e-13)
+    assert np.allclose(g3.reshape(-1, 3), g0[perm], atol=1e-12)
+
+
+def test_epsilon_sigma_scaling_law():
+    x = rand_cluster(9, 6)
+    e1, g1 = O.lj_energy_grad(x, 1.0, 1.0)
+    e2, g2 = O.lj_energy_grad(x, 2.5, 1.0)
+    assert e2 == pytest.approx(2.5 * e1, rel=1e-14)
+    assert np.allclose(g2, 2.5 * g1, rtol=1e-14, atol=0)
+    e3, g3 = O.lj_energy_grad(1.7 * x, 1.0, 1.7)
+    assert e3 == pytest.approx(e1, rel=1e-13)
+    assert np.allclose(g3, g1 / 1.7, rtol=1e-12, atol=1e-14)
+
+
+def test_degenerate_sizes_and_coincident_atoms():
+    e, g = O.lj_energy_grad(np.zeros(0))
+    assert e == 0.0 and g.size == 0
+    e, g = O.lj_energy_grad(np.array([1.0, 2.0, 3.0]))
+    assert e == 0.0 and np.all(g == 0)
+    e, g = O.lj_energy_grad(np.array([0.0, 0, 0, 0, 0, 0, 2, 0, 0]))
+    assert e == math.inf and np.all(np.isnan(g))
+    x, f, st, it, ne = O.minimize(np.array([0.0, 0, 0, 0, 0, 0, 2, 0, 0]))
+    assert st == O.NONFINITE and it == 0 and ne == 1
+
+
+# --------------------------------------------------------------------------
+# Minimiser pins
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,e_min", [(2, -1.0), (3, -3.0), (4, -6.0)])
+def test_brute_force_small_clusters_reach_unique_minimum(n, e_min):
+    for seed in range(8):
+        x0 = rand_cluster(n, 100 + seed, side=1.8, dmin=0.7)
+        x, f, st, it, _ = O.minimize(x0)
+        assert st == O.CONVERGED
+        assert f == pytest.approx(e_min, abs=1e-10)
+        _, g = O.lj_energy_grad(x)
+        assert np.abs(g).max() < 1e-6
+
+
+def test_quadratic_reaches_exact_solution():
+    rng = np.random.default_rng(11)
+    n = 24
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    lam = np.logspace(0, 2, n)
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    b = rng.normal(size=n)
+    xs = np.linalg.solve(A, b)
+    # gtol well above the FP64 resolution of f (|f| ~ 1): below ~1e-8 the
+    # decrease per step is under one ulp of f and no energy test can resolve it
+    p = O.MinParams(gtol=1e-7)
+    x, f, st, it, _ = O.minimize(np.zeros(n), kind=O.OBJ_QUADRATIC, params=p, A=A, b=b)
+    assert st == O.CONVERGED
+    # ||x - x*||_2 <= ||g||_2 / lambda_min
+    assert np.linalg.norm(x - xs) <= np.linalg.norm(A @ x - b) / lam.min() * (1 + 1e-6)
+    assert np.abs(A @ x - b).max() < 1e-7
+    assert f == pytest.approx(-0.5 * b @ xs, rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 10])
+def test_rosenbrock_reaches_ones(n):
+    x0 = np.tile([-1.2, 1.0], n // 2)
+    x, f, st, it, _ = O.minimize(x0, kind=O.OBJ_ROSENBROCK, params=O.MinParams(gtol=1e-9))
+    assert st == O.CONVERGED
+    assert np.abs(x - 1).max() < 1e-8
+    assert f < 1e-15
+
+
+def test_two_loop_equals_explicit_bfgs_inverse_recursion():
+    """N&W eq. (7.19): H_k from H_0 = gamma I by m BFGS inverse updates,
+    applied oldest first; the two-loop recursion must give -H_k g."""
+    rng = np.random.default_rng(3)
+    n, m = 9, 6
+    M = rng.normal(size=(n, n))
+    A = M @ M.T + n * np.eye(n)
+    S = rng.normal(size=(m, n))
+    Y = S @ A.T + 0.1 * rng.normal(size=(m, n))
+    assert np.all((S * Y).sum(1) > 0)
+    g = rng.normal(size=n)
+    gamma = S[-1] @ Y[-1] / (Y[-1] @ Y[-1])
+    H = gamma * np.eye(n)
+    for s, y in zip(S, Y):
+        rho = 1.0 / (s @ y)
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    d = O.lbfgs_direction(S, Y, g)
+    assert np.allclose(d, -H @ g, rtol=1e-11, atol=1e-12)
+    # with an empty history it is steepest descent
+    assert np.array_equal(O.lbfgs_direction(np.zeros((0, n)), np.zeros((0, n)), g), -g)
+
+
+def test_cubic_interpolation_exact_on_cubics():
+    # phi(a) = (a - 0.3)^2 (a + 2) has a local minimum at a = 0.3
+    phi = lambda a: (a - 0.3) ** 2 * (a + 2)
+    dphi = lambda a: 2 * (a - 0.3) * (a + 2) + (a - 0.3) ** 2
+    for a, b in [(0.0, 1.0), (1.0, 0.0), (0.1, 0.5)]:
+        t = O.cubic_interpolate(a, phi(a), dphi(a), b, phi(b), dphi(b))
+        assert t == pytest.approx(0.3, abs=1e-14)
+    # safeguard: result kept 10% inside the bracket
+    t = O.cubic_interpolate(0.0, phi(0.0), dphi(0.0), 0.31, phi(0.31), dphi(0.31))
+    assert t == pytest.approx(0.31 - 0.031, abs=1e-15)
+    # non-finite end -> midpoint
+    assert O.cubic_interpolate(0.0, 1.0, -1.0, 2.0, math.inf, 1.0) == 1.0
+
+
+def test_matches_scipy_lbfgsb_as_black_box():
+    """The paper's own minimiser (scipy L-BFGS-B, unbounded) from identical
+    starts: the same basin in most cases and the same energy there."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    n_same, n_tot = 0, 0
+    for seed in range(12):
+        x0 = rand_cluster(13, 200 + seed, side=2.6, dmin=0.8)
+        x, f, st, _, _ = O.minimize(x0)
+        assert st == O.CONVERGED
+        r = scipy_opt.minimize(lambda v: O.lj_energy_grad(v), x0, jac=True, method="L-BFGS-B",
+                               options=dict(maxcor=10, gtol=1e-6, ftol=0, maxiter=15000))
+        n_tot += 1
+        if abs(r.fun - f) < 1e-6:
+            n_same += 1
+    assert n_same >= 0.6 * n_tot
+
+
+def test_batch_drivers_agree_with_single_calls():
+    xs = inputs.cube_starts(6, 7, 2.2, seed=5)
+    sizes = np.array([7] * 6)
+    off = inputs.offsets_from_sizes(sizes)
+    e_u, g_u = O.eval_batch(xs, 6, uniform_n=7)
+    e_o, g_o = O.eval_batch(xs, 6, atom_off=off)
+    assert np.array_equal(e_u, e_o) and np.array_equal(g_u, g_o)
+    for c in range(6):
+        e, g = O.lj_energy_grad(xs[c])
+        assert e == e_u[c] and np.array_equal(g, g_u[3 * 7 * c:3 * 7 * (c + 1)])
+    xm, em, st, it, ne = O.lbfgs_batch(xs, 6, uniform_n=7, n_threads=3)
+    for c in range(6):
+        x, f, s1, i1, n1 = O.minimize(xs[c])
+        assert f == em[c] and s1 == st[c] and i1 == it[c] and n1 == ne[c]
+        assert np.array_equal(x, xm[21 * c:21 * (c + 1)])
+
+
+# --------------------------------------------------------------------------
+# Basin Hopping pins (Algorithm Overview steps 1, 3, 4, 5)
+# --------------------------------------------------------------------------
+def test_metropolis_rule():
+    assert O.metropolis(-5.0, -6.0, 0.8, 0.999999)       # downhill always
+    assert O.metropolis(-5.0, -5.0, 0.8, 0.999999)       # equal energy accepted
+    kT = 0.8
+    e_new = -5.0 + 0.3
+    de = e_new - (-5.0)
+    thr = math.exp(-de / kT)
+    assert O.metropolis(-5.0, e_new, kT, math.nextafter(thr, 0))
+    assert not O.metropolis(-5.0, e_new, kT, thr)
+    assert not O.metropolis(-5.0, e_new, 1e-30, 1e-300)
+
+
+def test_adaptation_rule():
+    f = 0.9
+    assert O.adapt_step(0.4, 10, 10, 0.5, f) == 0.4 / f      # all accepted: grow
+    assert O.adapt_step(0.4, 6, 10, 0.5, f) == 0.4 / f
+    assert O.adapt_step(0.4, 5, 10, 0.5, f) == 0.4 * f       # exactly target: shrink
+    assert O.adapt_step(0.4, 0, 10, 0.5, f) == 0.4 * f
+
+
+def _bh_state(x0, step0):
+    W, n3 = x0.shape
+    xm, em, st, _, _ = O.lbfgs_batch(x0, W, uniform_n=n3 // 3)
+    return {"x_cur": xm.reshape(W, n3).copy(), "e_cur": em.copy(),
+            "x_best": xm.reshape(W, n3).copy(), "e_best": em.copy(),
+            "stepsize": np.full(W, step0), "win_accept": np.zeros(W, np.int32),
+            "n_accept": np.zeros(W, np.int32)}
+
+
+def test_bh_trace_is_self_consistent():
+    x0 = inputs.cube_starts(3, 13, 2.0, seed=inputs.workload_seed(0))
+    st = _bh_state(x0, 0.4)
+    e_start = st["e_cur"].copy()
+    p = O.BhParamsPy(K=2, kT=0.8, n_steps=30, seed=99)
+    tr = O.bh_run(st, p)
+    for w in range(3):
+        e_cur = e_start[w]
+        step = 0.4
+        win = 0
+        best = e_start[w]
+        for s in range(30):
+            assert tr["stepsize"][s, w] == step
+            te = tr["trial_e"][s, w]
+            k = int(np.argmin(te))
+            assert tr["best_trial_e"][s, w] == te[k]
+            u = O.stream_uniform(99, 2, 0, 0, s, w)
+            acc = O.metropolis(e_cur, te[k], 0.8, u)
+            assert bool(tr["accepted"][s, w]) == acc
+            if acc:
+                e_cur = te[k]
+                win += 1
+                best = min(best, e_cur)
+            if (s + 1) % 10 == 0:
+                step = step / 0.9 if win / 10 > 0.5 else step * 0.9
+                win = 0
+        assert st["e_cur"][w] == e_cur and st["e_best"][w] == best
+        assert st["stepsize"][w] == step
+        assert st["n_accept"][w] == tr["accepted"][:, w].sum()
+
+
+def test_bh_first_step_moves_by_the_perturbation():
+    """With K = 1, no minimiser iterations and an infinite temperature, the
+    accepted structure is exactly the perturbed current structure."""
+    x0 = inputs.cube_starts(2, 6, 2.0, seed=3)
+    st = {"x_cur": x0.copy(), "e_cur": np.array([1e300, 1e300]), "x_best": x0.copy(),
+          "e_best": np.array([1e300, 1e300]), "stepsize": np.array([0.4, 0.25]),
+          "win_accept": np.zeros(2, np.int32), "n_accept": np.zeros(2, np.int32)}
+    p = O.BhParamsPy(K=1, kT=1e300, n_steps=1, seed=5, step0=17,
+                     min=O.MinParams(max_iter=0))
+    O.bh_run(st, p)
+    for w in range(2):
+        assert np.array_equal(st["x_cur"][w], O.perturb(x0[w], [0.4, 0.25][w], 5, 0, 17, w))
+
+
+def test_bh_holds_lj4_global_minimum():
+    x0 = inputs.cube_starts(2, 4, 1.6, seed=8)
+    st = _bh_state(x0, 0.3)
+    assert np.allclose(st["e_cur"], -6.0, atol=1e-10)
+    tr = O.bh_run(st, O.BhParamsPy(K=3, kT=0.8, n_steps=12, seed=1))
+    assert np.allclose(st["e_best"], -6.0, atol=1e-10)
+    assert np.all(tr["trial_e"] >= -6.0 - 1e-10)
