@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: batched LJ38 Basin Hopping on GB300 (one JSON line on stdout).
+
+Workload (one "step" = one Basin Hopping step of every walker): LJ38
+(eps = sigma = 1), 64 independent walkers x K = 8 candidates per step
+(512 local minimisations per step), starts uniform in a cube of side
+3.2 sigma (seeded), minimised once before timing; perturbations +-step per
+coordinate from Philox (initial step 0.4 sigma, adapted every 10 steps toward
+50% acceptance), kT = 0.8, L-BFGS m = 10 to ||grad E||_inf < 1e-6.
+
+metric  converged LJ minimisations per second (minimisations that reached
+        ||grad E||_inf < 1e-6 with an FP64 gradient), mixed precision path;
+        the FP64 path is measured on the same workload for comparison.
+Timing  CUDA events around each step's launch on the launching stream, L2
+        flushed (256 MiB write) between steps outside the events; e2e adds,
+        every step, the host->device copy of the walker state from pinned
+        memory and the device->host copy of the updated state.
+N > 1   (torchrun) each rank runs its own 64 walkers (global walker indices
+        offset by rank): weak scaling, no collective on the data path.
+--impl reference   the FP64 CPU oracle on this host's cores, same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ATOMS, WALKERS, K = 38, 64, 8
+SIDE, STEP0, KT = 3.2, 0.4, 0.8
+CONFIG_ID = 1
+WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per step (512 L-BFGS "
+            "minimisations per step), cube starts side 3.2 sigma, m=10, ||g||_inf<1e-6")
+PAIRS = N_ATOMS * (N_ATOMS - 1) // 2
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 (FMA) x max SM GHz
+FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def start_state(rank):
+    from paper_2510_25938_gb300 import inputs as I
+    seed = I.workload_seed(CONFIG_ID)
+    x0 = I.cube_starts(WALKERS * (rank + 1), N_ATOMS, SIDE, seed)[WALKERS * rank:]
+    return x0, seed
+
+
+def flops_from_stats(s):
+    """Algorithmic flops: 28 per unordered pair per evaluation, and per
+    L-BFGS iteration 8 * (history pairs used) * 3N (two dots + two axpys per
+    pair) + 12 * 3N for the remaining vector updates."""
+    pair = 28.0 * (s["pairs32"] + s["pairs64"])
+    vec = 8.0 * (s["vec_elems32"] + s["vec_elems64"]) + 12.0 * 3 * N_ATOMS * (
+        s["iters32"] + s["iters64"])
+    return pair + vec, 28.0 * s["pairs64"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_baseline(x0, seed, budget_s=12.0):
+    """The FP64 oracle on this host's cores: BH steps of all 64 walkers, as
+    many as fit in ~budget_s (at least one)."""
+    import oracle as O
+    xm, em, st, _, _ = O.lbfgs_batch(x0, x0.shape[0], uniform_n=N_ATOMS)
+    xm = xm.reshape(x0.shape[0], -1)
+    state = {"x_cur": xm.copy(), "e_cur": em.copy(), "x_best": xm.copy(), "e_best": em.copy(),
+             "stepsize": np.full(x0.shape[0], STEP0), "win_accept": np.zeros(x0.shape[0], np.int32),
+             "n_accept": np.zeros(x0.shape[0], np.int32)}
+    conv = mins = 0
+    steps = 0
+    t0 = time.perf_counter()
+    while steps == 0 or time.perf_counter() - t0 < budget_s:
+        tr = O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=steps, n_steps=1))
+        conv += int((tr["trial_status"] == O.CONVERGED).sum())
+        mins += tr["trial_status"].size
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": conv / dt, "unit": "converged minimisations/s", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} BH steps x 64 walkers x K=8 = {mins} FP64 minimisations of LJ38 "
+                      f"({conv} converged) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    x0, seed = start_state(0)
+    import oracle as O
+    xm, em, st, _, _ = O.lbfgs_batch(x0, WALKERS, uniform_n=N_ATOMS)
+    xm = xm.reshape(WALKERS, -1)
+    state = {"x_cur": xm.copy(), "e_cur": em.copy(), "x_best": xm.copy(), "e_best": em.copy(),
+             "stepsize": np.full(WALKERS, STEP0), "win_accept": np.zeros(WALKERS, np.int32),
+             "n_accept": np.zeros(WALKERS, np.int32)}
+    for s in range(args.warmup):
+        O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=s, n_steps=1))
+    conv = mins = 0
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        tr = O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=args.warmup + s,
+                                          n_steps=1))
+        conv += int((tr["trial_status"] == O.CONVERGED).sum())
+        mins += tr["trial_status"].size
+    dt = time.perf_counter() - t0
+    v = conv / dt
+    line = {"metric": "converged LJ minimisations/s", "value": v,
+            "unit": "converged minimisations/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": "converged minimisations/s",
+                             "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} BH steps x 64 walkers x K=8 = {mins} "
+                                       f"FP64 minimisations ({conv} converged)"},
+            "e2e": {"value": v, "unit": "converged minimisations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cuda(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2510_25938_gb300 import build as B
+    B.build()
+    from paper_2510_25938_gb300 import lj_bh as L
+
+    dev = torch.device("cuda", local)
+    ctx = L.Ctx(local)
+    ctx.reserve(WALKERS * K, N_ATOMS, 10)
+    x0, seed = start_state(rank)
+    walker0 = rank * WALKERS
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def init_state():
+        x = torch.as_tensor(x0.reshape(-1), dtype=torch.float64, device=dev).contiguous()
+        e = torch.empty(WALKERS, dtype=torch.float64, device=dev)
+        st = torch.empty(WALKERS, dtype=torch.int32, device=dev)
+        L.lbfgs_minimize_batched(ctx, x, e, st, n_cand=WALKERS, uniform_n=N_ATOMS,
+                                 params=L.LbfgsParams(prec=L.LJ_PREC_FP64))
+        xm = x.view(WALKERS, -1)
+        return {"x_cur": xm.clone(), "e_cur": e.clone(), "x_best": xm.clone(),
+                "e_best": e.clone(), "stepsize": torch.full((WALKERS,), STEP0, dtype=torch.float64,
+                                                            device=dev),
+                "win_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev),
+                "n_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev)}
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed_run(prec, n_steps, warmup):
+        state = init_state()
+        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=1, walker0=walker0,
+                       min=L.LbfgsParams(prec=prec))
+        for s in range(warmup):
+            p.step0 = s
+            L.bh_step_batched(ctx, state, p)
+        stats = L.new_stats(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n_steps)]
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for s in range(n_steps):
+                flush.fill_(float(s))
+                p.step0 = warmup + s
+                ev[s][0].record(stream)
+                L.bh_step_batched(ctx, state, p, None, stats)
+                ev[s][1].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return sum(ms) / 1e3, wall, L.stats_dict(stats), clk.summary(), state
+
+    def e2e_run(prec, n_steps, warmup):
+        """Public API with host buffers: pinned H2D of the walker state, the
+        BH step, D2H of the updated state, every step."""
+        dstate = init_state()
+        host = {k: v.cpu().pin_memory() for k, v in dstate.items()}
+        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=1, walker0=walker0,
+                       min=L.LbfgsParams(prec=prec))
+        stats = L.new_stats(dev)
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        for s in range(warmup + n_steps):
+            if s == warmup:
+                stats.zero_()
+                torch.cuda.synchronize()
+                barrier()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            for k in host:
+                dstate[k].copy_(host[k], non_blocking=True)
+            p.step0 = s
+            L.bh_step_batched(ctx, dstate, p, None, stats)
+            for k in host:
+                host[k].copy_(dstate[k], non_blocking=True)
+            torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        return wall, L.stats_dict(stats), h2d
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64)
+        torch.distributed.all_reduce(t)
+        return float(t.item())
+
+    # ---- mixed precision (headline) ----------------------------------------
+    t_dev, wall, st_mix, clocks, _ = timed_run(L.LJ_PREC_MIXED, args.steps, args.warmup)
+    t_dev = max_over_ranks(t_dev)
+    conv = sum_over_ranks(st_mix["converged"])
+    mins = sum_over_ranks(st_mix["minimisations"])
+    value = conv / t_dev
+    flops, flops64 = flops_from_stats(st_mix)
+    achieved_tf = flops / t_dev / 1e12 if world == 1 else None
+    # ---- FP64 path on the same workload --------------------------------------
+    n64 = args.fp64_steps if args.fp64_steps is not None else max(3, args.steps // 8)
+    t64, _, st64, _, _ = timed_run(L.LJ_PREC_FP64, n64, min(args.warmup, 3))
+    t64 = max_over_ranks(t64)
+    value64 = sum_over_ranks(st64["converged"]) / t64
+    flops_64path, _ = flops_from_stats(st64)
+    # ---- end to end -------------------------------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        wall_e2e, st_e2e, h2d = e2e_run(L.LJ_PREC_MIXED, max(5, args.steps // 4),
+                                        min(args.warmup, 3))
+        wall_e2e = max_over_ranks(wall_e2e)
+        e2e = {"value": sum_over_ranks(st_e2e["converged"]) / wall_e2e,
+               "unit": "converged minimisations/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": h2d}
+    line = {
+        "metric": "converged LJ minimisations/s",
+        "value": value,
+        "unit": "converged minimisations/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_atoms": N_ATOMS, "walkers_per_gpu": WALKERS, "K": K,
+                   "minimisations_per_step": WALKERS * K * world, "precision": "mixed",
+                   "l2": "flushed (256 MiB write) between timed steps"},
+        "minimisations_per_s": mins / t_dev,
+        "converged_fraction": conv / max(mins, 1),
+        "fp64_path": {"value": value64, "unit": "converged minimisations/s", "steps": n64,
+                      "ms_per_step": 1e3 * t64 / n64,
+                      "mixed_over_fp64": value / value64 if value64 > 0 else None,
+                      "achieved_tflops": flops_64path / t64 / 1e12,
+                      "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
+        "work": {k: st_mix[k] for k in ("evals32", "evals64", "iters32", "iters64")},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if achieved_tf is not None:
+        line["roofline"] = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
+                            "traffic": None, "kernel": "bh_kernel<32,2,mixed>",
+                            "fp64_flop_share": flops64 / flops if flops else None}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(x0, seed)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_cuda(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * lj_bh.h -- C ABI of the GB300 (sm_103a) batched Lennard-Jones local
+ * minimisation and Basin Hopping library (liblj_bh.so).
+ *
+ * Method: arXiv 2510.25938, "Revisiting and Accelerating the Basin Hopping
+ * Algorithm for Lennard-Jones Clusters".  The three compute entry points are
+ * the data-parallel hot path of that method:
+ *
+ *   lj_energy_grad_batched  -- Eq. (1) and its analytic gradient for a batch of
+ *                              clusters (Methodology, "Lennard-Jones Potential").
+ *   lbfgs_minimize_batched  -- local minimisation of many candidates at once
+ *                              (Methodology, "Algorithm Overview" step 2,
+ *                              "Parallel Evaluation of Candidates",
+ *                              "Implementation Notes": L-BFGS-B, read as
+ *                              unbounded L-BFGS, strong-Wolfe line search,
+ *                              ||grad E||_inf stopping rule).
+ *   bh_step_batched         -- whole Basin Hopping steps for many independent
+ *                              walkers: perturbation, K parallel minimisations,
+ *                              best-of-K selection, Metropolis test, step-size
+ *                              adaptation ("Algorithm Overview" steps 1-5).
+ *
+ * Conventions for every call:
+ *   - Coordinates are packed xyz per atom, atoms of a candidate contiguous,
+ *     candidates contiguous: the flattened 3N vector of the paper
+ *     ("Initial Structures and Input").  Row-major, no padding.
+ *   - Every d_* pointer is caller-owned DEVICE memory (e.g. torch tensors on
+ *     the ctx's device).  The library never frees or reallocates it.
+ *     Host-side structs (lj_batch, lj_*_params, lj_bh_state, lj_bh_trace)
+ *     are read during the call only and may be reused immediately.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  The return value covers argument
+ *     validation and launch errors only; per-candidate outcomes are written
+ *     to device status arrays (lj_cand_status).
+ *   - A ctx owns the workspace (L-BFGS history, work queue).  It is not
+ *     thread-safe: use one ctx per host thread / stream.  Calls on one ctx
+ *     that overlap on the GPU race on the workspace.
+ *   - After lj_ctx_reserve, calls within the reserved sizes allocate nothing
+ *     (safe inside CUDA-graph capture).  Without a reservation the ctx grows
+ *     its workspace on demand with cudaMalloc (not capture-safe); a call
+ *     beyond an explicit reservation returns LJ_ERR_NO_WORKSPACE.
+ *   - n_cand == 0 returns LJ_OK without a launch.  A candidate with 0 or 1
+ *     atoms has E = 0, gradient 0, status CONVERGED after 0 iterations.
+ *   - Coincident atoms (r = 0) or overflow give a non-finite energy; the
+ *     minimiser then reports LJ_CAND_NONFINITE for that candidate.
+ */
+#ifndef LJ_BH_H
+#define LJ_BH_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lj_ctx lj_ctx;
+
+typedef enum {
+    LJ_OK = 0,
+    LJ_ERR_INVALID_ARG = -1,   /* NULL pointer, negative size, bad enum, ... */
+    LJ_ERR_CUDA = -2,          /* a CUDA runtime call or launch failed */
+    LJ_ERR_NO_WORKSPACE = -3,  /* call exceeds lj_ctx_reserve sizes */
+    LJ_ERR_UNSUPPORTED = -4    /* valid but outside this build's limits */
+} lj_status;
+
+typedef enum { LJ_F32 = 0, LJ_F64 = 1 } lj_dtype;
+
+typedef enum {
+    LJ_PREC_FP64 = 0,   /* every operation in FP64 */
+    LJ_PREC_FP32 = 1,   /* evaluation only: FP32 pair terms, compensated energy */
+    LJ_PREC_MIXED = 2   /* minimisation: FP32 phase, then FP64 polish whose
+                           evaluations (x, gradient, energy) are FP64 and whose
+                           search directions stay FP32; the convergence test
+                           and returned energy are FP64 */
+} lj_precision;
+
+/* per-candidate outcome, written by the device */
+typedef enum {
+    LJ_CAND_CONVERGED = 0,       /* ||grad||_inf < gtol (FP64 gradient) */
+    LJ_CAND_MAXITER = 1,
+    LJ_CAND_LINESEARCH_FAIL = 2, /* no sufficient decrease, also along -grad */
+    LJ_CAND_NONFINITE = 3,       /* non-finite energy or gradient at the start */
+    LJ_CAND_TIMEOUT = 4,         /* deadline_cycles exceeded */
+    LJ_CAND_BAD_INPUT = 5        /* candidate larger than batch.max_n */
+} lj_cand_status;
+
+/* Library limits of this build. */
+#define LJ_MAX_ATOMS 1024        /* atoms per candidate */
+#define LJ_MAX_M 32              /* L-BFGS history length */
+#define LJ_MAX_K 32              /* candidates per walker and step */
+
+typedef struct {
+    int64_t n_cand;                /* number of candidates (>= 0) */
+    int32_t uniform_n;             /* > 0: every candidate has uniform_n atoms */
+    const int64_t* d_atom_offset;  /* uniform_n == 0: DEVICE int64[n_cand+1],
+                                      exclusive scan of atom counts */
+    int32_t max_n;                 /* uniform_n == 0: upper bound on atoms per
+                                      candidate (<= LJ_MAX_ATOMS) */
+} lj_batch;
+
+typedef struct {
+    int32_t m;               /* history length, 1..LJ_MAX_M (10 in the paper's setting) */
+    double gtol;             /* stop when ||grad E||_inf < gtol (1e-6) */
+    int32_t max_iter;        /* iteration cap (15000) */
+    int32_t max_ls;          /* energy evaluations per line search (20) */
+    double c1, c2;           /* strong-Wolfe constants (1e-3, 0.9) */
+    double alpha_max;        /* largest trial step (1e10) */
+    lj_precision prec;       /* LJ_PREC_FP64 or LJ_PREC_MIXED */
+    double switch_gtol;      /* MIXED: FP32 phase ends once ||g32||_inf < switch_gtol */
+    int64_t deadline_cycles; /* > 0: a candidate still running after this many
+                                SM clock cycles stops with LJ_CAND_TIMEOUT */
+    double eps, sigma;       /* LJ parameters of Eq. (1) (1, 1) */
+} lj_lbfgs_params;
+
+typedef struct {
+    int32_t K;               /* candidates per walker and step, 1..LJ_MAX_K */
+    double kT;               /* Metropolis temperature in energy units */
+    double target_rate;      /* acceptance rate the adaptation aims at (0.5) */
+    int32_t interval;        /* adapt after every `interval` global steps (10) */
+    double factor;           /* rate > target: step /= factor, else step *= factor */
+    uint64_t seed;           /* Philox key */
+    int64_t step0;           /* global index of the first step of this call */
+    int32_t n_steps;         /* steps done by this call (>= 0) */
+    int64_t walker0;         /* global index of walker 0 (for sharding) */
+    lj_lbfgs_params min;     /* local minimiser */
+} lj_bh_params;
+
+/* Walker state, DEVICE arrays, updated in place.  All walkers share n_atoms. */
+typedef struct {
+    int32_t n_walkers;
+    int32_t n_atoms;
+    double* x_cur;     /* [W][3N] current (minimised) structure */
+    double* e_cur;     /* [W] its FP64 energy */
+    double* x_best;    /* [W][3N] lowest-energy accepted structure */
+    double* e_best;    /* [W] */
+    double* stepsize;  /* [W] perturbation half-width */
+    int32_t* win_accept; /* [W] acceptances in the current adaptation window */
+    int32_t* n_accept;   /* [W] total acceptances */
+} lj_bh_state;
+
+/* Optional per-step trace, DEVICE arrays; any pointer may be NULL. */
+typedef struct {
+    double* trial_e;        /* [n_steps][W][K] minimised candidate energies */
+    int32_t* trial_status;  /* [n_steps][W][K] lj_cand_status */
+    int32_t* trial_iters;   /* [n_steps][W][K] L-BFGS iterations */
+    double* best_trial_e;   /* [n_steps][W] energy of the selected candidate */
+    uint8_t* accepted;      /* [n_steps][W] Metropolis outcome */
+    double* stepsize;       /* [n_steps][W] step size used in that step */
+} lj_bh_trace;
+
+/* Device-side work counters, accumulated (atomically) by a call; the caller
+ * zeroes them.  Used for flop accounting and throughput. */
+typedef struct {
+    unsigned long long evals32;     /* FP32 energy+gradient evaluations */
+    unsigned long long evals64;     /* FP64 energy+gradient evaluations */
+    unsigned long long iters32;     /* L-BFGS iterations in the FP32 phase */
+    unsigned long long iters64;     /* L-BFGS iterations in FP64 / polish */
+    unsigned long long pairs32;     /* unordered atom pairs evaluated in FP32 */
+    unsigned long long pairs64;     /* unordered atom pairs evaluated in FP64 */
+    unsigned long long vec_elems32; /* sum over iterations of m_used * 3N (FP32 vectors) */
+    unsigned long long vec_elems64; /* same for FP64 vectors */
+    unsigned long long converged;   /* candidates with LJ_CAND_CONVERGED */
+    unsigned long long minimisations; /* candidates minimised */
+} lj_stats;
+
+const char* lj_status_string(lj_status s);
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+lj_status lj_ctx_create(lj_ctx** out, int device);
+/* Destroy a context and free its workspace (synchronises its device). */
+lj_status lj_ctx_destroy(lj_ctx* ctx);
+/* Reserve workspace for calls with up to max_cand candidates (or walkers x K
+ * for bh_step_batched) of up to max_n atoms and history length max_m.  After
+ * a reservation no call allocates. */
+lj_status lj_ctx_reserve(lj_ctx* ctx, int64_t max_cand, int32_t max_n, int32_t max_m);
+/* Human-readable description of the last error on this ctx ("" if none). */
+const char* lj_ctx_last_error(const lj_ctx* ctx);
+
+/*
+ * Eq. (1) energy (FP64 result) and gradient for every candidate of `batch`.
+ *   prec   LJ_PREC_FP32 (or MIXED): FP32 pair terms with compensated energy
+ *          accumulation; LJ_PREC_FP64: every operation in FP64.
+ *   xtype  dtype of d_x and d_grad (LJ_F32 or LJ_F64).
+ *   d_x    [total_atoms*3] coordinates.
+ *   d_energy [n_cand] FP64 energies.
+ *   d_grad [total_atoms*3] gradient dE/dx in xtype, or NULL for energy only.
+ *   eps, sigma  Eq. (1) parameters (> 0).
+ */
+lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
+                                 lj_dtype xtype, const void* d_x, double* d_energy,
+                                 void* d_grad, double eps, double sigma, void* stream);
+
+/*
+ * Local minimisation of every candidate of `batch`, in place.
+ *   d_x      [total_atoms*3] FP64 start coordinates in, minimised out.
+ *   d_energy [n_cand] FP64 energy at the returned coordinates.
+ *   d_status [n_cand] lj_cand_status (may be NULL).
+ *   d_iters  [n_cand] L-BFGS iterations (may be NULL).
+ *   d_nevals [n_cand] energy+gradient evaluations (may be NULL).
+ *   d_stats  device lj_stats accumulated by this call (may be NULL).
+ */
+lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lbfgs_params* p,
+                                 double* d_x, double* d_energy, int32_t* d_status,
+                                 int32_t* d_iters, int32_t* d_nevals, lj_stats* d_stats,
+                                 void* stream);
+
+/*
+ * p->n_steps Basin Hopping steps for every walker of `state`, in one launch.
+ * Step s (global index step0 + i) of walker w (global walker0 + w):
+ *   1. K candidates x_k = x_cur + step * (2u - 1) per coordinate, u from
+ *      Philox4x32-10 stream 1 at counter (coordinate, k, s, w);
+ *   2. each candidate minimised as in lbfgs_minimize_batched;
+ *   3. k* = lowest finite energy (ties: lowest k);
+ *   4. accept if E_k* <= E_cur or u < exp(-(E_k* - E_cur)/kT), u from stream 2;
+ *   5. after step s with (s+1) % interval == 0: window rate > target_rate ->
+ *      step /= factor, else step *= factor; window counter reset.
+ * state must hold minimised structures with their energies (e.g. from
+ * lbfgs_minimize_batched).  trace and d_stats may be NULL.
+ */
+lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_params* p,
+                          const lj_bh_trace* trace, lj_stats* d_stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) batched Lennard-Jones local minimisation and Basin Hopping.
+
+``paper_2510_25938_gb300.lj_bh`` is the ctypes binding of the CUDA library
+(include/lj_bh.h); ``paper_2510_25938_gb300.inputs`` makes seeded synthetic
+starting structures; ``paper_2510_25938_gb300.build`` compiles the library.
+Nothing is imported eagerly, so the input generators work without torch/CUDA.
+"""

@@ -1,0 +1,328 @@
+// lj_api.cu -- the C ABI of include/lj_bh.h: context, workspace, argument
+// validation and kernel dispatch.  Host code only.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <cuda_runtime.h>
+
+#include "../../include/lj_bh.h"
+#include "lj_internal.h"
+
+struct lj_ctx {
+  int device = 0;
+  int sms = 0;
+  void* ws = nullptr;                  // L-BFGS history workspace
+  size_t ws_bytes = 0;
+  bool reserved = false;
+  unsigned long long* queue = nullptr; // persistent-kernel work counter
+  std::string last_error;
+};
+
+namespace {
+
+// Makes ctx->device current for the scope of one call, then restores.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+lj_status fail(lj_ctx* ctx, lj_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+lj_status cuda_fail(lj_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, LJ_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// history bytes per team slot for a given atom bound (largest team variant
+// of that bound, FP64 history) -- used only to size reservations
+size_t slot_bytes_bound(int max_n, int m) {
+  int T = 32, A = 1;
+  if (max_n > 32) A = 2;
+  if (max_n > 64) T = 64;
+  if (max_n > 128) T = 128;
+  if (max_n > 256) T = 256;
+  if (max_n > 512) T = 512;
+  return (2 * (size_t)m * A * 3 * T * sizeof(double) + 15) & ~size_t(15);
+}
+
+lj_status ensure_ws(lj_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return LJ_OK;
+  if (ctx->reserved) {
+    return fail(ctx, LJ_ERR_NO_WORKSPACE,
+                "call needs " + std::to_string(bytes) + " workspace bytes, reserved " +
+                    std::to_string(ctx->ws_bytes));
+  }
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace cudaMalloc");
+  ctx->ws_bytes = bytes;
+  return LJ_OK;
+}
+
+lj_status check_batch(lj_ctx* ctx, const lj_batch* b, int* max_n) {
+  if (!b) return fail(ctx, LJ_ERR_INVALID_ARG, "batch is NULL");
+  if (b->n_cand < 0) return fail(ctx, LJ_ERR_INVALID_ARG, "n_cand < 0");
+  if (b->uniform_n < 0) return fail(ctx, LJ_ERR_INVALID_ARG, "uniform_n < 0");
+  if (b->uniform_n > 0) {
+    *max_n = b->uniform_n;
+  } else {
+    if (b->n_cand > 0 && !b->d_atom_offset)
+      return fail(ctx, LJ_ERR_INVALID_ARG, "uniform_n == 0 needs d_atom_offset");
+    if (b->max_n < 0) return fail(ctx, LJ_ERR_INVALID_ARG, "max_n < 0");
+    if (b->d_atom_offset && !aligned(b->d_atom_offset, 8))
+      return fail(ctx, LJ_ERR_INVALID_ARG, "d_atom_offset misaligned");
+    *max_n = b->max_n;
+  }
+  if (*max_n > LJ_MAX_ATOMS)
+    return fail(ctx, LJ_ERR_UNSUPPORTED,
+                "clusters of " + std::to_string(*max_n) + " atoms exceed LJ_MAX_ATOMS");
+  if (*max_n < 1) *max_n = 1;
+  return LJ_OK;
+}
+
+lj_status check_min(lj_ctx* ctx, const lj_lbfgs_params* p) {
+  if (!p) return fail(ctx, LJ_ERR_INVALID_ARG, "params is NULL");
+  if (p->m < 1 || p->m > LJ_MAX_M) return fail(ctx, LJ_ERR_INVALID_ARG, "m outside 1..LJ_MAX_M");
+  if (!(p->gtol > 0.0)) return fail(ctx, LJ_ERR_INVALID_ARG, "gtol must be > 0");
+  if (p->max_iter < 0) return fail(ctx, LJ_ERR_INVALID_ARG, "max_iter < 0");
+  if (p->max_ls < 1) return fail(ctx, LJ_ERR_INVALID_ARG, "max_ls < 1");
+  if (!(p->c1 > 0.0 && p->c1 < p->c2 && p->c2 < 1.0))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "need 0 < c1 < c2 < 1");
+  if (!(p->alpha_max > 0.0)) return fail(ctx, LJ_ERR_INVALID_ARG, "alpha_max must be > 0");
+  if (p->prec != LJ_PREC_FP64 && p->prec != LJ_PREC_MIXED)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "minimisation precision must be FP64 or MIXED");
+  if (p->prec == LJ_PREC_MIXED && !(p->switch_gtol > 0.0))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "switch_gtol must be > 0");
+  if (!(p->eps > 0.0 && std::isfinite(p->eps) && p->sigma > 0.0 && std::isfinite(p->sigma)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "eps and sigma must be finite and > 0");
+  return LJ_OK;
+}
+
+ljh::MinParamsH to_host(const lj_lbfgs_params* p) {
+  ljh::MinParamsH h;
+  h.m = p->m; h.max_iter = p->max_iter; h.max_ls = p->max_ls;
+  h.gtol = p->gtol; h.c1 = p->c1; h.c2 = p->c2; h.alpha_max = p->alpha_max;
+  h.switch_gtol = p->switch_gtol; h.deadline = p->deadline_cycles;
+  h.eps = p->eps; h.sigma = p->sigma;
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lj_status_string(lj_status s) {
+  switch (s) {
+    case LJ_OK: return "LJ_OK";
+    case LJ_ERR_INVALID_ARG: return "LJ_ERR_INVALID_ARG";
+    case LJ_ERR_CUDA: return "LJ_ERR_CUDA";
+    case LJ_ERR_NO_WORKSPACE: return "LJ_ERR_NO_WORKSPACE";
+    case LJ_ERR_UNSUPPORTED: return "LJ_ERR_UNSUPPORTED";
+  }
+  return "LJ_STATUS_UNKNOWN";
+}
+
+lj_status lj_ctx_create(lj_ctx** out, int device) {
+  if (!out) return LJ_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return LJ_ERR_INVALID_ARG;
+  lj_ctx* c = new (std::nothrow) lj_ctx();
+  if (!c) return LJ_ERR_CUDA;
+  c->device = device;
+  DeviceGuard g(device);
+  if (!g.ok) { delete c; return LJ_ERR_CUDA; }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->queue, 64) != cudaSuccess) { delete c; return LJ_ERR_CUDA; }
+  *out = c;
+  return LJ_OK;
+}
+
+lj_status lj_ctx_destroy(lj_ctx* ctx) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->queue) cudaFree(ctx->queue);
+  }
+  delete ctx;
+  return LJ_OK;
+}
+
+lj_status lj_ctx_reserve(lj_ctx* ctx, int64_t max_cand, int32_t max_n, int32_t max_m) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  if (max_cand < 0 || max_n < 0 || max_m < 1 || max_m > LJ_MAX_M)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "bad reservation sizes");
+  if (max_n > LJ_MAX_ATOMS) return fail(ctx, LJ_ERR_UNSUPPORTED, "max_n > LJ_MAX_ATOMS");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  const int64_t slots = max_cand < 4 ? 4 : max_cand;
+  const size_t bytes = (size_t)slots * slot_bytes_bound(max_n < 1 ? 1 : max_n, max_m);
+  ctx->reserved = false;
+  lj_status st = ensure_ws(ctx, bytes);
+  if (st != LJ_OK) return st;
+  ctx->reserved = true;
+  return LJ_OK;
+}
+
+const char* lj_ctx_last_error(const lj_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "NULL ctx";
+}
+
+lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
+                                 lj_dtype xtype, const void* d_x, double* d_energy, void* d_grad,
+                                 double eps, double sigma, void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  int max_n = 0;
+  lj_status st = check_batch(ctx, batch, &max_n);
+  if (st != LJ_OK) return st;
+  if (prec != LJ_PREC_FP64 && prec != LJ_PREC_FP32 && prec != LJ_PREC_MIXED)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "bad precision");
+  if (xtype != LJ_F32 && xtype != LJ_F64) return fail(ctx, LJ_ERR_INVALID_ARG, "bad dtype");
+  if (!(eps > 0.0 && std::isfinite(eps) && sigma > 0.0 && std::isfinite(sigma)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "eps and sigma must be finite and > 0");
+  if (batch->n_cand == 0) return LJ_OK;
+  if (!d_x || !d_energy) return fail(ctx, LJ_ERR_INVALID_ARG, "d_x and d_energy are required");
+  const size_t el = xtype == LJ_F32 ? 4 : 8;
+  if (!aligned(d_x, el) || !aligned(d_energy, 8) || (d_grad && !aligned(d_grad, el)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "misaligned pointer");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  ljh::EvalArgs a;
+  a.n_cand = batch->n_cand;
+  a.uniform_n = batch->uniform_n;
+  a.off = batch->d_atom_offset;
+  a.max_n = max_n;
+  a.xtype = xtype;
+  a.prec = prec;
+  a.x = d_x;
+  a.energy = d_energy;
+  a.grad = d_grad;
+  a.eps = eps;
+  a.sigma = sigma;
+  cudaError_t e = ljh::eval_launch(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lj_energy_grad_batched launch");
+  return LJ_OK;
+}
+
+lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lbfgs_params* p,
+                                 double* d_x, double* d_energy, int32_t* d_status,
+                                 int32_t* d_iters, int32_t* d_nevals, lj_stats* d_stats,
+                                 void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  int max_n = 0;
+  lj_status st = check_batch(ctx, batch, &max_n);
+  if (st != LJ_OK) return st;
+  st = check_min(ctx, p);
+  if (st != LJ_OK) return st;
+  if (batch->n_cand == 0) return LJ_OK;
+  if (!d_x || !d_energy) return fail(ctx, LJ_ERR_INVALID_ARG, "d_x and d_energy are required");
+  if (!aligned(d_x, 8) || !aligned(d_energy, 8) || (d_status && !aligned(d_status, 4)) ||
+      (d_iters && !aligned(d_iters, 4)) || (d_nevals && !aligned(d_nevals, 4)) ||
+      (d_stats && !aligned(d_stats, 8)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "misaligned pointer");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  const int mixed = p->prec == LJ_PREC_MIXED;
+  ljh::Plan plan;
+  cudaError_t e = ljh::lbfgs_plan(max_n, p->m, mixed, batch->n_cand, ctx->device, &plan);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched plan");
+  st = ensure_ws(ctx, (size_t)plan.slots * plan.slot_bytes);
+  if (st != LJ_OK) return st;
+  ljh::LbfgsArgs a;
+  a.n_cand = batch->n_cand;
+  a.uniform_n = batch->uniform_n;
+  a.off = batch->d_atom_offset;
+  a.max_n = max_n;
+  a.p = to_host(p);
+  a.mixed = mixed;
+  a.x = d_x;
+  a.energy = d_energy;
+  a.status = d_status;
+  a.iters = d_iters;
+  a.nevals = d_nevals;
+  a.stats = d_stats;
+  a.queue = ctx->queue;
+  a.hist = ctx->ws;
+  a.hist_slot_bytes = plan.slot_bytes;
+  e = ljh::lbfgs_launch(a, plan, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
+  return LJ_OK;
+}
+
+lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params* p,
+                          const lj_bh_trace* trace, lj_stats* d_stats, void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  if (!s || !p) return fail(ctx, LJ_ERR_INVALID_ARG, "state and params are required");
+  lj_status st = check_min(ctx, &p->min);
+  if (st != LJ_OK) return st;
+  if (s->n_walkers < 0 || s->n_atoms < 0) return fail(ctx, LJ_ERR_INVALID_ARG, "negative sizes");
+  if (p->K < 1 || p->K > LJ_MAX_K) return fail(ctx, LJ_ERR_INVALID_ARG, "K outside 1..LJ_MAX_K");
+  if (!(p->kT > 0.0)) return fail(ctx, LJ_ERR_INVALID_ARG, "kT must be > 0");
+  if (p->interval < 1) return fail(ctx, LJ_ERR_INVALID_ARG, "interval < 1");
+  if (!(p->factor > 0.0 && std::isfinite(p->factor)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "factor must be finite and > 0");
+  if (p->n_steps < 0) return fail(ctx, LJ_ERR_INVALID_ARG, "n_steps < 0");
+  if (s->n_walkers == 0 || p->n_steps == 0) return LJ_OK;
+  if (!s->x_cur || !s->e_cur || !s->x_best || !s->e_best || !s->stepsize || !s->win_accept ||
+      !s->n_accept)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "every state array is required");
+  if (!aligned(s->x_cur, 8) || !aligned(s->x_best, 8) || !aligned(s->e_cur, 8) ||
+      !aligned(s->e_best, 8) || !aligned(s->stepsize, 8) || !aligned(s->win_accept, 4) ||
+      !aligned(s->n_accept, 4) || (d_stats && !aligned(d_stats, 8)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "misaligned pointer");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  const int mixed = p->min.prec == LJ_PREC_MIXED;
+  ljh::Plan plan;
+  cudaError_t e = ljh::bh_plan(s->n_atoms, p->min.m, mixed, s->n_walkers, p->K, &plan);
+  if (e == cudaErrorNotSupported)
+    return fail(ctx, LJ_ERR_UNSUPPORTED,
+                "bh_step_batched supports K * team_size <= 256 and N <= 256 in this build");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bh_step_batched plan");
+  st = ensure_ws(ctx, (size_t)plan.slots * plan.slot_bytes);
+  if (st != LJ_OK) return st;
+  ljh::BhArgs a;
+  a.n_walkers = s->n_walkers;
+  a.n_atoms = s->n_atoms;
+  a.x_cur = s->x_cur; a.e_cur = s->e_cur; a.x_best = s->x_best; a.e_best = s->e_best;
+  a.stepsize = s->stepsize; a.win_accept = s->win_accept; a.n_accept = s->n_accept;
+  a.K = p->K; a.kT = p->kT; a.target_rate = p->target_rate; a.factor = p->factor;
+  a.interval = p->interval; a.seed = p->seed; a.step0 = p->step0; a.n_steps = p->n_steps;
+  a.walker0 = p->walker0;
+  a.p = to_host(&p->min);
+  a.mixed = mixed;
+  if (trace) {
+    a.tr = *trace;
+  } else {
+    std::memset(&a.tr, 0, sizeof(a.tr));
+  }
+  a.stats = d_stats;
+  a.hist = ctx->ws;
+  a.hist_slot_bytes = plan.slot_bytes;
+  e = ljh::bh_launch(a, plan, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bh_step_batched launch");
+  return LJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,365 @@
+// lj_device.cuh -- sm_103a device building blocks: teams, team reductions,
+// Philox4x32-10, float-float energies and the Eq. (1) pair loops.
+//
+// A "team" is the group of T threads that owns one candidate cluster:
+// one warp (T = 32) or a multiple of 32 threads synchronised by a named
+// barrier.  Thread `rank` of a team owns atoms rank, rank + T, ... (A slots)
+// and exactly the 3 coordinates / gradient components of those atoms, so
+// every vector operation of L-BFGS is thread-local and only the pair loop
+// reads other threads' atoms (from shared memory).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ljd {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+enum : int32_t {
+  ST_CONVERGED = 0, ST_MAXITER = 1, ST_LS_FAIL = 2, ST_NONFINITE = 3, ST_TIMEOUT = 4,
+  ST_BAD_INPUT = 5
+};
+
+// ---------------------------------------------------------------------------
+// Team
+// ---------------------------------------------------------------------------
+template <int T>
+struct Team {
+  static_assert(T % 32 == 0 && T >= 32 && T <= 1024, "team size");
+  int rank;       // 0 .. T-1
+  int bar;        // named barrier id (T > 32); 1..15
+  double* red;    // shared scratch for cross-warp reductions: 8 * (T/32) doubles
+  __device__ __forceinline__ void sync() const {
+    if constexpr (T == 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(T) : "memory");
+    }
+  }
+};
+
+template <typename V>
+__device__ __forceinline__ V shfl_xor(V v, int o) { return __shfl_xor_sync(kFull, v, o); }
+
+// Sum of NV values over the team; every thread receives the same bits
+// (xor butterfly: partners add the same operands; the cross-warp stage sums
+// the per-warp results in the same order on every thread).
+template <int T, int NV, typename V>
+__device__ __forceinline__ void team_sum(const Team<T>& tm, V (&v)[NV]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += shfl_xor(v[k], o);
+  }
+  if constexpr (T > 32) {
+    static_assert(NV * sizeof(V) <= 8 * sizeof(double), "reduction scratch");
+    constexpr int NW = T / 32;
+    V* buf = reinterpret_cast<V*>(tm.red);
+    tm.sync();
+    if ((tm.rank & 31) == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) buf[(tm.rank >> 5) * NV + k] = v[k];
+    }
+    tm.sync();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      V s = buf[k];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) s += buf[w * NV + k];
+      v[k] = s;
+    }
+  }
+}
+
+template <int T, typename V>
+__device__ __forceinline__ V team_sum1(const Team<T>& tm, V x) {
+  V v[1] = {x};
+  team_sum<T, 1, V>(tm, v);
+  return v[0];
+}
+
+// Max over the team (inputs are >= 0; a non-finite entry must be passed as +inf).
+template <int T, int NV, typename V>
+__device__ __forceinline__ void team_max(const Team<T>& tm, V (&v)[NV]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = fmax(v[k], shfl_xor(v[k], o));
+  }
+  if constexpr (T > 32) {
+    constexpr int NW = T / 32;
+    V* buf = reinterpret_cast<V*>(tm.red);
+    tm.sync();
+    if ((tm.rank & 31) == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) buf[(tm.rank >> 5) * NV + k] = v[k];
+    }
+    tm.sync();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      V s = buf[k];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) s = fmax(s, buf[w * NV + k]);
+      v[k] = s;
+    }
+  }
+}
+
+// |x| with NaN mapped to +inf, so that fmax-based norms flag non-finite input
+__device__ __forceinline__ float abs_nan_inf(float x) {
+  return (x != x) ? __int_as_float(0x7f800000) : fabsf(x);
+}
+__device__ __forceinline__ double abs_nan_inf(double x) {
+  return (x != x) ? __longlong_as_double(0x7ff0000000000000LL) : fabs(x);
+}
+
+// ---------------------------------------------------------------------------
+// Float-float energy values (FP32 phase): hi + lo, |lo| <= ulp(hi)/2.
+// The FP32 phase keeps its energies in this form so that the line search can
+// form energy differences without any FP64 instruction.
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return ff{s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return ff_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  ff s = ff_two_sum(a.hi, b);
+  return ff_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_scale(ff a, float c) {   // c exact power of two or
+  return ff{a.hi * c, a.lo * c};                          // small integer: near-exact
+}
+
+// energy-value traits: difference, finiteness, conversion
+__device__ __forceinline__ float fdiff(ff a, ff b) {
+  return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+__device__ __forceinline__ double fdiff(double a, double b) { return a - b; }
+__device__ __forceinline__ bool fisfinite(ff a) { return isfinite(a.hi); }
+__device__ __forceinline__ bool fisfinite(double a) { return isfinite(a); }
+__device__ __forceinline__ double fto_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double fto_double(double a) { return a; }
+
+template <int T>
+__device__ __forceinline__ ff team_sum_ff(const Team<T>& tm, ff v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ff w{shfl_xor(v.hi, o), shfl_xor(v.lo, o)};
+    v = ff_add(v, w);
+  }
+  if constexpr (T > 32) {
+    constexpr int NW = T / 32;
+    float* buf = reinterpret_cast<float*>(tm.red);
+    tm.sync();
+    if ((tm.rank & 31) == 0) {
+      buf[2 * (tm.rank >> 5)] = v.hi;
+      buf[2 * (tm.rank >> 5) + 1] = v.lo;
+    }
+    tm.sync();
+    ff s{buf[0], buf[1]};
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s = ff_add(s, ff{buf[2 * w], buf[2 * w + 1]});
+    v = s;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from the published round
+// function and key schedule, and the 53-bit uniform built from two words.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u01_53(uint32_t a, uint32_t b) {
+  const double hi = (double)(a >> 5);
+  const double lo = (double)(b >> 6);
+  return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 1.0 / 9007199254740992.0);
+}
+
+// uniform number `draw` of stream `tag` at counter (k, s, w)
+__device__ __forceinline__ double stream_u01(uint64_t seed, uint32_t tag, uint32_t draw,
+                                             uint32_t k, uint32_t s, uint32_t w) {
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ tag);
+  const uint4 r = philox4x32_10(make_uint4(draw >> 1, k, s, w), key);
+  return (draw & 1u) ? u01_53(r.z, r.w) : u01_53(r.x, r.y);
+}
+
+// ---------------------------------------------------------------------------
+// Pair loops of Eq. (1).  One-sided form: the thread owning atom i sums over
+// every j != i, so no two threads write the same gradient entry and the
+// result is deterministic.  Per owned atom it returns
+//   acc_i = sum_j s2 s6 (2 s6 - 1) (x_i - x_j),  e_i = sum_j s6 (s6 - 1)
+// with s2 = sigma^2 / r^2, s6 = s2^3; then grad_i = -(24 eps / sigma^2) acc_i
+// and E = 2 eps sum_i e_i (every unordered pair is visited twice).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+struct alignas(16) PosF { float x, y, z, w; };
+struct alignas(16) PosD { double x, y, z, w; };
+
+template <typename X> struct PosOf;
+template <> struct PosOf<float> { using type = PosF; };
+template <> struct PosOf<double> { using type = PosD; };
+
+// FP32: 4-term blocks summed in FP32, folded into a float-float accumulator.
+__device__ __forceinline__ void pair_row_f32(int n, int i, float px, float py, float pz,
+                                             const PosF* __restrict__ pos, float sig2,
+                                             float& ax, float& ay, float& az, ff& e) {
+  ax = 0.f; ay = 0.f; az = 0.f;
+  int j = 0;
+  for (; j + 4 <= n; j += 4) {
+    float eb = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const PosF q = pos[j + u];
+      const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float ir2 = (j + u == i) ? 0.f : rcp_approx(r2);
+      const float s2 = sig2 * ir2;
+      const float s6 = s2 * s2 * s2;
+      const float t = s6 - 1.f;
+      eb = fmaf(s6, t, eb);
+      const float c = (s2 * s6) * (s6 + t);
+      ax = fmaf(c, dx, ax);
+      ay = fmaf(c, dy, ay);
+      az = fmaf(c, dz, az);
+    }
+    e = ff_add_f(e, eb);
+  }
+  float eb = 0.f;
+  for (; j < n; ++j) {
+    const PosF q = pos[j];
+    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir2 = (j == i) ? 0.f : rcp_approx(r2);
+    const float s2 = sig2 * ir2;
+    const float s6 = s2 * s2 * s2;
+    const float t = s6 - 1.f;
+    eb = fmaf(s6, t, eb);
+    const float c = (s2 * s6) * (s6 + t);
+    ax = fmaf(c, dx, ax);
+    ay = fmaf(c, dy, ay);
+    az = fmaf(c, dz, az);
+  }
+  e = ff_add_f(e, eb);
+}
+
+// Double-double helpers: exact sum a + b = s + e (Knuth TwoSum).
+struct dd {
+  double hi, lo;
+};
+__device__ __forceinline__ dd dd_two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  const double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return dd{s, e};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  return dd_two_sum(s.hi, __dadd_rn(s.lo, __dadd_rn(a.lo, b.lo)));
+}
+
+template <int T>
+__device__ __forceinline__ double team_sum_dd(const Team<T>& tm, dd v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd w{shfl_xor(v.hi, o), shfl_xor(v.lo, o)};
+    v = dd_add(v, w);
+  }
+  if constexpr (T > 32) {
+    constexpr int NW = T / 32;
+    double* buf = tm.red;
+    tm.sync();
+    if ((tm.rank & 31) == 0) {
+      buf[2 * (tm.rank >> 5)] = v.hi;
+      buf[2 * (tm.rank >> 5) + 1] = v.lo;
+    }
+    tm.sync();
+    dd s{buf[0], buf[1]};
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s = dd_add(s, dd{buf[2 * w], buf[2 * w + 1]});
+    v = s;
+  }
+  return __dadd_rn(v.hi, v.lo);
+}
+
+// FP64: the reciprocal is the correctly rounded one; the energy is summed in
+// 4-term blocks folded into a compensated (double-double) accumulator, so
+// that near a minimum its rounding noise stays below the decreases the
+// line search must resolve (|E| ~ 170 for LJ38, decreases ~1e-12).
+__device__ __forceinline__ void pair_row_f64(int n, int i, double px, double py, double pz,
+                                             const PosD* __restrict__ pos, double sig2,
+                                             double& ax, double& ay, double& az, dd& e) {
+  ax = 0.0; ay = 0.0; az = 0.0;
+  int j = 0;
+  for (; j + 4 <= n; j += 4) {
+    double eb = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const PosD q = pos[j + u];
+      const double dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+      const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      const double ir2 = (j + u == i) ? 0.0 : __drcp_rn(r2);
+      const double s2 = sig2 * ir2;
+      const double s6 = s2 * s2 * s2;
+      const double t = s6 - 1.0;
+      eb = fma(s6, t, eb);
+      const double c = (s2 * s6) * (s6 + t);
+      ax = fma(c, dx, ax);
+      ay = fma(c, dy, ay);
+      az = fma(c, dz, az);
+    }
+    dd s = dd_two_sum(e.hi, eb);
+    e.hi = s.hi;
+    e.lo = __dadd_rn(e.lo, s.lo);
+  }
+  double eb = 0.0;
+  for (; j < n; ++j) {
+    const PosD q = pos[j];
+    const double dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double ir2 = (j == i) ? 0.0 : __drcp_rn(r2);
+    const double s2 = sig2 * ir2;
+    const double s6 = s2 * s2 * s2;
+    const double t = s6 - 1.0;
+    eb = fma(s6, t, eb);
+    const double c = (s2 * s6) * (s6 + t);
+    ax = fma(c, dx, ax);
+    ay = fma(c, dy, ay);
+    az = fma(c, dz, az);
+  }
+  dd s = dd_two_sum(e.hi, eb);
+  e.hi = s.hi;
+  e.lo = __dadd_rn(e.lo, s.lo);
+}
+
+}  // namespace ljd

@@ -1,0 +1,88 @@
+// lj_internal.h -- host-side interface between the C-ABI layer (lj_api.cu)
+// and the kernel translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/lj_bh.h"
+
+namespace ljd { struct MinParams; }
+
+namespace ljh {
+
+struct MinParamsH {     // mirror of ljd::MinParams (plain data)
+  int m, max_iter, max_ls;
+  double gtol, c1, c2, alpha_max, switch_gtol;
+  long long deadline;
+  double eps, sigma;
+};
+
+struct EvalArgs {
+  int64_t n_cand;
+  int uniform_n;
+  const int64_t* off;
+  int max_n;
+  int xtype;            // LJ_F32 / LJ_F64
+  int prec;             // LJ_PREC_*
+  const void* x;
+  double* energy;
+  void* grad;
+  double eps, sigma;
+};
+
+struct LbfgsArgs {
+  int64_t n_cand;
+  int uniform_n;
+  const int64_t* off;
+  int max_n;
+  MinParamsH p;
+  int mixed;
+  double* x;
+  double* energy;
+  int32_t* status;
+  int32_t* iters;
+  int32_t* nevals;
+  lj_stats* stats;
+  unsigned long long* queue;   // zeroed before the launch
+  void* hist;
+  size_t hist_slot_bytes;
+};
+
+struct BhArgs {
+  int n_walkers, n_atoms;
+  double *x_cur, *e_cur, *x_best, *e_best, *stepsize;
+  int32_t *win_accept, *n_accept;
+  int K;
+  double kT, target_rate, factor;
+  int interval;
+  unsigned long long seed;
+  long long step0;
+  int n_steps;
+  long long walker0;
+  MinParamsH p;
+  int mixed;
+  lj_bh_trace tr;
+  lj_stats* stats;
+  void* hist;
+  size_t hist_slot_bytes;
+};
+
+struct Plan {
+  int team;          // threads per team
+  int teams_per_cta;
+  int grid;          // CTAs
+  size_t smem;       // dynamic shared memory per CTA
+  int64_t slots;     // history slots the launch needs
+  size_t slot_bytes; // bytes per history slot
+};
+
+// largest atom count this build supports
+constexpr int kMaxAtoms = LJ_MAX_ATOMS;
+
+cudaError_t eval_launch(const EvalArgs& a, cudaStream_t s);
+cudaError_t lbfgs_plan(int max_n, int m, int mixed, int64_t n_cand, int device, Plan* out);
+cudaError_t lbfgs_launch(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t bh_plan(int n_atoms, int m, int mixed, int n_walkers, int K, Plan* out);
+cudaError_t bh_launch(const BhArgs& a, const Plan& plan, cudaStream_t s);
+
+}  // namespace ljh

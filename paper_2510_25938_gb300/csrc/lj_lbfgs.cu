@@ -1,0 +1,163 @@
+// lj_lbfgs.cu -- lbfgs_minimize_batched: a persistent kernel in which every
+// team takes candidates from a device work queue (one atomic counter) and
+// runs the whole L-BFGS loop on chip -- direction, line search, convergence
+// test -- with no host round trip per iteration.  Candidates converge after
+// different iteration counts; the queue keeps every team busy until the
+// batch is drained.
+#include "lj_internal.h"
+#include "lj_minimize.cuh"
+#include "lj_teams.cuh"
+
+namespace {
+
+using namespace ljd;
+
+__device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
+  MinParams p;
+  p.m = h.m; p.max_iter = h.max_iter; p.max_ls = h.max_ls;
+  p.gtol = h.gtol; p.c1 = h.c1; p.c2 = h.c2; p.alpha_max = h.alpha_max;
+  p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.eps = h.eps; p.sigma = h.sigma;
+  return p;
+}
+
+template <int T, int A, bool MIXED>
+__global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int TPC = cta_threads_for(T) / T;
+  const int team = threadIdx.x / T;
+  Team<T> tm;
+  tm.rank = threadIdx.x % T;
+  tm.bar = team + 1;
+  void* pos;
+  long long* word;
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n), a.max_n, pos, tm.red, word);
+  const MinParams p = to_dev(a.p);
+  const long long slot = (long long)blockIdx.x * TPC + team;
+  void* hist = static_cast<unsigned char*>(a.hist) + slot * a.hist_slot_bytes;
+
+  for (;;) {
+    long long c;
+    if constexpr (T == 32) {
+      unsigned long long v = 0;
+      if (tm.rank == 0) v = atomicAdd(a.queue, 1ULL);
+      c = (long long)__shfl_sync(kFull, v, 0);
+    } else {
+      if (tm.rank == 0) *word = (long long)atomicAdd(a.queue, 1ULL);
+      tm.sync();
+      c = *word;
+      tm.sync();
+    }
+    if (c >= a.n_cand) break;
+    long long a0;
+    int n;
+    if (a.uniform_n > 0) {
+      a0 = c * a.uniform_n;
+      n = a.uniform_n;
+    } else {
+      a0 = a.off[c];
+      n = (int)(a.off[c + 1] - a0);
+    }
+    if (n > a.max_n || n < 0) {
+      if (tm.rank == 0) {
+        a.energy[c] = __longlong_as_double(0x7ff8000000000000LL);
+        if (a.status) a.status[c] = ST_BAD_INPUT;
+        if (a.iters) a.iters[c] = 0;
+        if (a.nevals) a.nevals[c] = 0;
+      }
+      continue;
+    }
+    double x64[A][3];
+#pragma unroll
+    for (int s = 0; s < A; ++s) {
+      const int i = tm.rank + s * T;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) x64[s][k] = i < n ? a.x[3 * (a0 + i) + k] : 0.0;
+    }
+    MinResult r;
+    minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, r);
+#pragma unroll
+    for (int s = 0; s < A; ++s) {
+      const int i = tm.rank + s * T;
+      if (i < n) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.x[3 * (a0 + i) + k] = x64[s][k];
+      }
+    }
+    if (tm.rank == 0) {
+      a.energy[c] = r.E;
+      if (a.status) a.status[c] = r.status;
+      if (a.iters) a.iters[c] = r.iters;
+      if (a.nevals) a.nevals[c] = r.evals32 + r.evals64;
+      if (a.stats) {
+        const unsigned long long np = (unsigned long long)n * (unsigned long long)(n > 0 ? n - 1 : 0) / 2;
+        atomicAdd(&a.stats->evals32, (unsigned long long)r.evals32);
+        atomicAdd(&a.stats->evals64, (unsigned long long)r.evals64);
+        atomicAdd(&a.stats->iters32, (unsigned long long)r.iters32);
+        atomicAdd(&a.stats->iters64, (unsigned long long)r.iters64);
+        atomicAdd(&a.stats->pairs32, np * (unsigned long long)r.evals32);
+        atomicAdd(&a.stats->pairs64, np * (unsigned long long)r.evals64);
+        atomicAdd(&a.stats->vec_elems32, (unsigned long long)r.vec32);
+        atomicAdd(&a.stats->vec_elems64, (unsigned long long)r.vec64);
+        atomicAdd(&a.stats->converged, r.status == ST_CONVERGED ? 1ULL : 0ULL);
+        atomicAdd(&a.stats->minimisations, 1ULL);
+      }
+    }
+  }
+}
+
+template <int T, int A, bool MIXED>
+cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out) {
+  constexpr int threads = cta_threads_for(T);
+  constexpr int TPC = threads / T;
+  const size_t smem = TPC * team_smem_bytes<T>(max_n);
+  auto k = lbfgs_kernel<T, A, MIXED>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long need = (n_cand + TPC - 1) / TPC;
+  long long grid = (long long)per_sm * sms;
+  if (need < grid) grid = need;
+  if (grid < 1) grid = 1;
+  out->team = T;
+  out->teams_per_cta = TPC;
+  out->grid = (int)grid;
+  out->smem = smem;
+  out->slots = grid * TPC;
+  out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
+  return cudaSuccess;
+}
+
+}  // namespace
+
+namespace ljh {
+
+cudaError_t lbfgs_plan(int max_n, int m, int mixed, int64_t n_cand, int device, Plan* out) {
+  return dispatch_team(max_n, [&](auto TT, auto AA) -> cudaError_t {
+    constexpr int T = decltype(TT)::value;
+    constexpr int A = decltype(AA)::value;
+    return mixed ? plan_one<T, A, true>(max_n, m, n_cand, device, out)
+                 : plan_one<T, A, false>(max_n, m, n_cand, device, out);
+  });
+}
+
+cudaError_t lbfgs_launch(const LbfgsArgs& a, const Plan& plan, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  return dispatch_team(a.max_n, [&](auto TT, auto AA) -> cudaError_t {
+    constexpr int T = decltype(TT)::value;
+    constexpr int A = decltype(AA)::value;
+    const int threads = cta_threads_for(T);
+    if (a.mixed) {
+      lbfgs_kernel<T, A, true><<<plan.grid, threads, plan.smem, s>>>(a);
+    } else {
+      lbfgs_kernel<T, A, false><<<plan.grid, threads, plan.smem, s>>>(a);
+    }
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace ljh

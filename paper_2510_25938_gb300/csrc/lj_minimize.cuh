@@ -1,0 +1,510 @@
+// lj_minimize.cuh -- one team minimises one LJ cluster with L-BFGS.
+//
+// Method (arXiv 2510.25938, Methodology, "Algorithm Overview" step 2 and
+// "Implementation Notes": L-BFGS-B from scipy, no bounds), read as:
+//   direction   two-loop recursion, H0 = (s^T y / y^T y) I of the newest pair
+//               (Nocedal & Wright Alg. 7.4); steepest descent when the
+//               history is empty or the direction is not a descent direction;
+//   first trial alpha = min(1, 1/||d||_2) with an empty history, else 1;
+//   line search strong Wolfe, c1 = 1e-3, c2 = 0.9, bracketing with doubling
+//               (N&W Alg. 3.5) and zoom with safeguarded cubic interpolation
+//               (N&W Alg. 3.6, eq. 3.59); a non-finite energy fails the
+//               sufficient-decrease test; after max_ls evaluations the best
+//               sufficient-decrease point is taken if it strictly lowers E;
+//               on failure one retry along -g with an empty history;
+//   curvature   the pair (s, y) is stored only if s^T y > eps_mach y^T y;
+//   stopping    ||g||_inf < gtol after each accepted step (and at the start).
+//
+// Precision (GB300: FP64 issues ~1/62 of FP32, the FP64 reciprocal less):
+//   FP64 path   every operation in FP64.
+//   MIXED path  phase 1: coordinates, gradient, directions and history in
+//               FP32, energy as float-float, line-search scalars in FP32, no
+//               FP64 instruction at all; it ends when ||g32||_inf <
+//               switch_gtol, when the predicted decrease falls below the FP32
+//               energy resolution, or when its line search fails.
+//               phase 2 (polish): coordinates, gradient and energy in FP64
+//               (FP64 pair terms); directions and history stay FP32 (they
+//               only steer); the stopping test uses the FP64 gradient.
+#pragma once
+#include "lj_device.cuh"
+#include "../../include/lj_bh.h"
+
+namespace ljd {
+
+struct MinParams {
+  int m, max_iter, max_ls;
+  double gtol, c1, c2, alpha_max, switch_gtol;
+  long long deadline;
+  double eps, sigma;
+};
+
+struct MinResult {
+  double E;
+  int status;
+  int iters;
+  int evals32, evals64, iters32, iters64;
+  long long vec32, vec64;   // sum over iterations of (history used) * 3N
+};
+
+enum : int { PH_CONVERGED = 0, PH_MAXITER = 1, PH_LSFAIL = 2, PH_SWITCH = 3, PH_TIMEOUT = 4 };
+
+template <typename X> struct Tr;
+template <> struct Tr<float> { using S = float; using F = ff; };
+template <> struct Tr<double> { using S = double; using F = double; };
+
+template <typename V> __device__ __forceinline__ V eps_mach();
+template <> __device__ __forceinline__ float eps_mach<float>() { return 1.1920928955078125e-7f; }
+template <> __device__ __forceinline__ double eps_mach<double>() { return 2.220446049250313e-16; }
+
+__device__ __forceinline__ float S_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double S_sqrt(double x) { return sqrt(x); }
+
+// history element (slot, atom slot a, component c) of this thread
+template <int T, int A>
+__device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
+  return ((slot * A + a) * 3 + c) * T + rank;
+}
+
+// ---------------------------------------------------------------------------
+// Energy and gradient at x (owned atoms), and dphi = g . d when d != nullptr.
+// ---------------------------------------------------------------------------
+template <int T, int A, typename X, typename V>
+__device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[A][3], X (&g)[A][3],
+                                         typename PosOf<X>::type* pos, const MinParams& p,
+                                         const V (*d)[3], typename Tr<X>::F& E,
+                                         typename Tr<X>::S& dphi) {
+  using S = typename Tr<X>::S;
+  const X sig2 = (X)(p.sigma * p.sigma);
+  const X gscale = (X)(24.0 * p.eps / (p.sigma * p.sigma));
+  tm.sync();  // previous readers of pos are done
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int i = tm.rank + a * T;
+    if (i < n) {
+      typename PosOf<X>::type q;
+      q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
+      pos[i] = q;
+    }
+  }
+  tm.sync();
+  V dp = (V)0;
+  if constexpr (sizeof(X) == 4) {
+    ff e{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int i = tm.rank + a * T;
+      if (i < n) {
+        float ax, ay, az;
+        ff ea{0.f, 0.f};
+        pair_row_f32(n, i, x[a][0], x[a][1], x[a][2], pos, sig2, ax, ay, az, ea);
+        g[a][0] = -gscale * ax; g[a][1] = -gscale * ay; g[a][2] = -gscale * az;
+        e = ff_add(e, ea);
+      } else {
+        g[a][0] = 0.f; g[a][1] = 0.f; g[a][2] = 0.f;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    ff et = team_sum_ff<T>(tm, e);
+    E = ff_scale(et, (float)(2.0 * p.eps));
+  } else {
+    dd e{0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int i = tm.rank + a * T;
+      if (i < n) {
+        double ax, ay, az;
+        pair_row_f64(n, i, x[a][0], x[a][1], x[a][2], pos, sig2, ax, ay, az, e);
+        g[a][0] = -gscale * ax; g[a][1] = -gscale * ay; g[a][2] = -gscale * az;
+      } else {
+        g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    E = team_sum_dd<T>(tm, e) * (2.0 * p.eps);
+  }
+  if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+}
+
+template <int T, int A, typename X>
+__device__ __forceinline__ X grad_max(const Team<T>& tm, const X (&g)[A][3]) {
+  X m = (X)0;
+#pragma unroll
+  for (int a = 0; a < A; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m = fmax(m, abs_nan_inf(g[a][c]));
+  X v[1] = {m};
+  team_max<T, 1, X>(tm, v);
+  return v[0];
+}
+
+// safeguarded cubic interpolation (N&W eq. 3.59), kept 10% inside the bracket
+template <typename S, typename F>
+__device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
+  const S lo = a < b ? a : b;
+  const S hi = a < b ? b : a;
+  const S w = hi - lo;
+  const S mid = (S)0.5 * (a + b);
+  if (!(fisfinite(fa) && fisfinite(fb) && isfinite(ga) && isfinite(gb))) return mid;
+  const S d1 = ga + gb - (S)3 * ((S)fdiff(fa, fb) / (a - b));
+  const S disc = d1 * d1 - ga * gb;
+  if (!(disc >= (S)0)) return mid;
+  S d2 = S_sqrt(disc);
+  if (b - a < (S)0) d2 = -d2;
+  const S den = gb - ga + (S)2 * d2;
+  if (den == (S)0) return mid;
+  S t = b - (b - a) * ((gb + d2 - d1) / den);
+  if (!isfinite(t)) return mid;
+  const S tlo = lo + (S)0.1 * w;
+  const S thi = hi - (S)0.1 * w;
+  if (t < tlo) t = tlo;
+  if (t > thi) t = thi;
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// One L-BFGS phase: iterate from (x, g, f) until a stop condition.
+// X: coordinates/gradient precision, V: direction/history precision.
+// F32PHASE: the mixed path's FP32 phase (never declares convergence).
+// ---------------------------------------------------------------------------
+template <int T, int A, typename X, typename V, bool F32PHASE>
+__device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
+                         typename Tr<X>::F& f, V* __restrict__ Sh, V* __restrict__ Yh,
+                         V (&sy)[LJ_MAX_M], V (&yy)[LJ_MAX_M], int& cnt, int& head, int& iters,
+                         int& evals, int& phase_iters, long long& vec, typename PosOf<X>::type* pos,
+                         const MinParams& p, long long t0) {
+  using S = typename Tr<X>::S;
+  using F = typename Tr<X>::F;
+  const int m = p.m;
+  const S c1 = (S)p.c1, c2 = (S)p.c2, amax = (S)p.alpha_max;
+  const X stop_gtol = F32PHASE ? (X)p.switch_gtol : (X)p.gtol;
+  V alpha[LJ_MAX_M];
+  V d[A][3];
+  X xt[A][3], gt[A][3];
+
+  while (iters < p.max_iter) {
+    // ---- search direction -------------------------------------------------
+    S dphi0 = (S)1;
+    if (cnt > 0) {
+      V q[A][3];
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[a][c] = (V)g[a][c];
+      for (int t = cnt - 1; t >= 0; --t) {
+        int slot = head + t;
+        if (slot >= m) slot -= m;
+        V part = (V)0;
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) part += Sh[hidx<T, A>(slot, a, c, tm.rank)] * q[a][c];
+        const V rho = (V)1 / sy[slot];
+        const V al = rho * team_sum1<T, V>(tm, part);
+        alpha[t] = al;
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q[a][c] -= al * Yh[hidx<T, A>(slot, a, c, tm.rank)];
+      }
+      int newest = head + cnt - 1;
+      if (newest >= m) newest -= m;
+      const V gam = sy[newest] / yy[newest];
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[a][c] *= gam;
+      for (int t = 0; t < cnt; ++t) {
+        int slot = head + t;
+        if (slot >= m) slot -= m;
+        V part = (V)0;
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) part += Yh[hidx<T, A>(slot, a, c, tm.rank)] * q[a][c];
+        const V rho = (V)1 / sy[slot];
+        const V coef = alpha[t] - rho * team_sum1<T, V>(tm, part);
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q[a][c] += coef * Sh[hidx<T, A>(slot, a, c, tm.rank)];
+      }
+      V part = (V)0;
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          d[a][c] = -q[a][c];
+          part += (V)g[a][c] * d[a][c];
+        }
+      dphi0 = (S)team_sum1<T, V>(tm, part);
+      vec += (long long)cnt * 3 * n;
+    }
+    if (!(dphi0 < (S)0)) {  // empty history or not a descent direction
+      cnt = 0;
+      head = 0;
+      V part = (V)0;
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          d[a][c] = -(V)g[a][c];
+          part += d[a][c] * d[a][c];
+        }
+      dphi0 = -(S)team_sum1<T, V>(tm, part);
+    }
+    bool ok = false;
+    F ft;
+    for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+      if (attempt == 1) {
+        if (cnt == 0) break;  // already steepest descent: no retry
+        cnt = 0;
+        head = 0;
+        V part = (V)0;
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            d[a][c] = -(V)g[a][c];
+            part += d[a][c] * d[a][c];
+          }
+        dphi0 = -(S)team_sum1<T, V>(tm, part);
+      }
+      S a1 = (S)1;
+      if (cnt == 0) {
+        a1 = (S)1 / S_sqrt(-dphi0);
+        if (a1 > (S)1) a1 = (S)1;
+      }
+      if constexpr (F32PHASE) {
+        // predicted decrease below ~8 ulp of the FP32 energy: hand over to FP64
+        if (-dphi0 * a1 < (S)4.76837158203125e-7 * fabsf(f.hi)) return PH_SWITCH;
+      }
+      // ---- strong-Wolfe line search ----------------------------------------
+      int ev = 0;
+      S a_prev = (S)0, dp_prev = dphi0;
+      F f_prev = f;
+      S a = a1;
+      bool have_best = false;
+      S best_a = (S)0, last_a = (S)-1;
+      F best_f = f;
+      S lo = 0, hi = 0, dp_lo = 0, dp_hi = 0;
+      F f_lo = f, f_hi = f;
+      S dp;
+      bool done = false, zoom = false;
+      auto trial = [&](S al, F& fo, S& dpo) {
+#pragma unroll
+        for (int aa = 0; aa < A; ++aa)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) xt[aa][c] = x[aa][c] + (X)al * (X)d[aa][c];
+        evaluate<T, A, X, V>(tm, n, xt, gt, pos, p, d, fo, dpo);
+        ++ev;
+        last_a = al;
+      };
+      for (int i = 1; !done && !zoom; ++i) {
+        if (ev >= p.max_ls) break;
+        F fa;
+        trial(a, fa, dp);
+        const bool armijo = fisfinite(fa) && ((S)fdiff(fa, f) <= c1 * a * dphi0);
+        if (armijo && (!have_best || (S)fdiff(fa, best_f) < (S)0)) {
+          have_best = true; best_f = fa; best_a = a;
+        }
+        if (!armijo || (i > 1 && (S)fdiff(fa, f_prev) >= (S)0)) {
+          lo = a_prev; f_lo = f_prev; dp_lo = dp_prev;
+          hi = a; f_hi = fa; dp_hi = dp;
+          zoom = true;
+        } else if (fabs(dp) <= -c2 * dphi0) {
+          ft = fa; done = true;
+        } else if (dp >= (S)0) {
+          lo = a; f_lo = fa; dp_lo = dp;
+          hi = a_prev; f_hi = f_prev; dp_hi = dp_prev;
+          zoom = true;
+        } else {
+          a_prev = a; f_prev = fa; dp_prev = dp;
+          a = (S)2 * a;
+          if (a > amax) a = amax;
+        }
+      }
+      while (zoom && !done) {
+        if (ev >= p.max_ls) break;
+        const S aj = cubic_step<S, F>(lo, f_lo, dp_lo, hi, f_hi, dp_hi);
+        F fa;
+        trial(aj, fa, dp);
+        const bool armijo = fisfinite(fa) && ((S)fdiff(fa, f) <= c1 * aj * dphi0);
+        if (armijo && (!have_best || (S)fdiff(fa, best_f) < (S)0)) {
+          have_best = true; best_f = fa; best_a = aj;
+        }
+        if (!armijo || (S)fdiff(fa, f_lo) >= (S)0) {
+          hi = aj; f_hi = fa; dp_hi = dp;
+        } else {
+          if (fabs(dp) <= -c2 * dphi0) {
+            ft = fa; done = true;
+          } else {
+            if (dp * (hi - lo) >= (S)0) {
+              hi = lo; f_hi = f_lo; dp_hi = dp_lo;
+            }
+            lo = aj; f_lo = fa; dp_lo = dp;
+          }
+        }
+      }
+      if (!done && have_best && (S)fdiff(best_f, f) < (S)0) {
+        if (last_a != best_a) {
+          F fa;
+          trial(best_a, fa, dp);
+          ft = fa;
+        } else {
+          ft = best_f;
+        }
+        done = true;
+      }
+      evals += ev;
+      ok = done;
+    }
+    if (!ok) return F32PHASE ? PH_SWITCH : PH_LSFAIL;
+
+    // ---- curvature pair, then move ------------------------------------------
+    V sv[A][3], yv[A][3];
+    V pr[2] = {(V)0, (V)0};
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sv[a][c] = (V)(xt[a][c] - x[a][c]);
+        yv[a][c] = (V)(gt[a][c] - g[a][c]);
+        pr[0] += sv[a][c] * yv[a][c];
+        pr[1] += yv[a][c] * yv[a][c];
+      }
+    team_sum<T, 2, V>(tm, pr);
+    if (pr[0] > eps_mach<V>() * pr[1]) {
+      int slot;
+      if (cnt < m) {
+        slot = head + cnt;
+        if (slot >= m) slot -= m;
+        ++cnt;
+      } else {
+        slot = head;
+        head = head + 1 == m ? 0 : head + 1;
+      }
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Sh[hidx<T, A>(slot, a, c, tm.rank)] = sv[a][c];
+          Yh[hidx<T, A>(slot, a, c, tm.rank)] = yv[a][c];
+        }
+      sy[slot] = pr[0];
+      yy[slot] = pr[1];
+    }
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x[a][c] = xt[a][c];
+        g[a][c] = gt[a][c];
+      }
+    f = ft;
+    ++iters;
+    ++phase_iters;
+    // ---- stopping tests ----------------------------------------------------
+    X mv[2];
+    mv[0] = (X)0;
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mv[0] = fmax(mv[0], abs_nan_inf(g[a][c]));
+    mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (X)1 : (X)0;
+    team_max<T, 2, X>(tm, mv);
+    if (mv[0] < stop_gtol) return F32PHASE ? PH_SWITCH : PH_CONVERGED;
+    if (mv[1] > (X)0) return PH_TIMEOUT;
+  }
+  return PH_MAXITER;
+}
+
+// ---------------------------------------------------------------------------
+// Minimise the cluster whose owned coordinates are in x64 (in place).
+// hist: this team's history slot (2 m A 3 T values of the phase's V type).
+// pos:  this team's shared position buffer (n PosD entries).
+// ---------------------------------------------------------------------------
+template <int T, int A, bool MIXED>
+__device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const MinParams& p,
+                         void* hist, void* pos, MinResult& r) {
+  r.E = 0.0; r.status = ST_CONVERGED; r.iters = 0;
+  r.evals32 = 0; r.evals64 = 0; r.iters32 = 0; r.iters64 = 0; r.vec32 = 0; r.vec64 = 0;
+  if (n <= 1) return;
+  const long long t0 = clock64();
+  int cnt = 0, head = 0, iters = 0;
+  const size_t hstride = (size_t)p.m * A * 3 * T;
+  if constexpr (!MIXED) {
+    double g[A][3];
+    double f, dummy;
+    evaluate<T, A, double, double>(tm, n, x64, g, (PosD*)pos, p, nullptr, f, dummy);
+    r.evals64 = 1;
+    const double gm = grad_max<T, A, double>(tm, g);
+    if (!isfinite(f) || !(gm < __longlong_as_double(0x7ff0000000000000LL))) {
+      r.E = f; r.status = ST_NONFINITE; return;
+    }
+    if (gm < p.gtol) { r.E = f; return; }
+    double sy[LJ_MAX_M], yy[LJ_MAX_M];
+    double* Sh = (double*)hist;
+    const int code = run_phase<T, A, double, double, false>(
+        tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt, head, iters, r.evals64, r.iters64,
+        r.vec64, (PosD*)pos, p, t0);
+    r.E = f;
+    r.iters = iters;
+    r.status = code == PH_CONVERGED ? ST_CONVERGED
+             : code == PH_LSFAIL   ? ST_LS_FAIL
+             : code == PH_TIMEOUT  ? ST_TIMEOUT : ST_MAXITER;
+  } else {
+    float* Sh = (float*)hist;
+    float* Yh = Sh + hstride;
+    float sy[LJ_MAX_M], yy[LJ_MAX_M];
+    int code = PH_SWITCH;
+    {
+      float x32[A][3], g32[A][3];
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x32[a][c] = (float)x64[a][c];
+      ff f32;
+      float dummy;
+      evaluate<T, A, float, float>(tm, n, x32, g32, (PosF*)pos, p, nullptr, f32, dummy);
+      r.evals32 = 1;
+      const float gm = grad_max<T, A, float>(tm, g32);
+      if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
+        code = run_phase<T, A, float, float, true>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt,
+                                                   head, iters, r.evals32, r.iters32, r.vec32,
+                                                   (PosF*)pos, p, t0);
+        if (r.iters32 > 0) {
+#pragma unroll
+          for (int a = 0; a < A; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
+        }
+      }
+    }
+    // FP64 evaluation at the hand-over point (also the final energy when the
+    // FP32 phase ran out of iterations or time)
+    double g[A][3];
+    double f, dummy;
+    evaluate<T, A, double, double>(tm, n, x64, g, (PosD*)pos, p, nullptr, f, dummy);
+    r.evals64 += 1;
+    const double gm = grad_max<T, A, double>(tm, g);
+    r.E = f;
+    if (!isfinite(f) || !(gm < __longlong_as_double(0x7ff0000000000000LL))) {
+      r.status = ST_NONFINITE;
+    } else if (gm < p.gtol) {
+      r.status = ST_CONVERGED;
+    } else if (code == PH_MAXITER || code == PH_TIMEOUT) {
+      r.status = code == PH_MAXITER ? ST_MAXITER : ST_TIMEOUT;
+    } else {
+      code = run_phase<T, A, double, float, false>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
+                                                   iters, r.evals64, r.iters64, r.vec64,
+                                                   (PosD*)pos, p, t0);
+      r.E = f;
+      r.status = code == PH_CONVERGED ? ST_CONVERGED
+               : code == PH_LSFAIL   ? ST_LS_FAIL
+               : code == PH_TIMEOUT  ? ST_TIMEOUT : ST_MAXITER;
+    }
+    r.iters = iters;
+  }
+}
+
+}  // namespace ljd

@@ -1,0 +1,45 @@
+// lj_teams.cuh -- team-size variants and per-team shared-memory carving,
+// shared by the kernel translation units.
+#pragma once
+#include <type_traits>
+#include <cuda_runtime.h>
+#include "lj_device.cuh"
+
+namespace ljd {
+
+// Team size T and atom slots per thread A for clusters of up to max_n atoms.
+// Thread `rank` owns atoms rank + a*T, a < A.
+template <class F>
+__host__ cudaError_t dispatch_team(int max_n, F&& f) {
+  using std::integral_constant;
+  if (max_n <= 32) return f(integral_constant<int, 32>{}, integral_constant<int, 1>{});
+  if (max_n <= 64) return f(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+  if (max_n <= 128) return f(integral_constant<int, 64>{}, integral_constant<int, 2>{});
+  if (max_n <= 256) return f(integral_constant<int, 128>{}, integral_constant<int, 2>{});
+  if (max_n <= 512) return f(integral_constant<int, 256>{}, integral_constant<int, 2>{});
+  if (max_n <= 1024) return f(integral_constant<int, 512>{}, integral_constant<int, 2>{});
+  return cudaErrorInvalidValue;
+}
+
+__host__ __device__ constexpr int cta_threads_for(int T) { return T < 128 ? 128 : T; }
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// per-team shared bytes: positions (as FP64 quads; the FP32 phase uses the
+// first half of the same buffer), cross-warp reduction scratch, one word
+template <int T>
+__host__ __device__ constexpr size_t team_smem_bytes(int max_n) {
+  return align16((size_t)max_n * sizeof(PosD)) + (T > 32 ? 8 * (T / 32) * sizeof(double) : 0) + 16;
+}
+
+template <int T>
+__device__ __forceinline__ void carve_team(unsigned char* base, int max_n, void*& pos, double*& red,
+                                           long long*& word) {
+  pos = base;
+  unsigned char* p = base + align16((size_t)max_n * sizeof(PosD));
+  red = reinterpret_cast<double*>(p);
+  p += (T > 32 ? 8 * (T / 32) * sizeof(double) : 0);
+  word = reinterpret_cast<long long*>(p);
+}
+
+}  // namespace ljd

@@ -1,0 +1,47 @@
+"""Test-side property checks (independent of both the oracle and the CUDA path).
+
+* fingerprint: sorted pair distances of a cluster -- invariant under
+  translation, rotation, reflection and permutation; two minima are the same
+  basin when their fingerprints agree to 1e-3 sigma (max abs difference).
+* numpy_energy_grad: vectorised Eq. (1) energy and gradient, used only to
+  check properties of returned minima (||g||_inf, E(x) consistency).
+* grad_scale: the no-cancellation gradient scale ||(sum_j |c_ij d_ij|)_i||_2,
+  the denominator that keeps relative gradient errors meaningful near minima.
+"""
+import numpy as np
+
+SAME_BASIN_TOL = 1e-3
+
+
+def fingerprint(x):
+    p = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    d = np.sqrt(((p[:, None, :] - p[None, :, :]) ** 2).sum(-1))
+    return np.sort(d[np.triu_indices(len(p), 1)])
+
+
+def same_basin(xa, xb, tol=SAME_BASIN_TOL):
+    fa, fb = fingerprint(xa), fingerprint(xb)
+    return fa.shape == fb.shape and (fa.size == 0 or np.abs(fa - fb).max() <= tol)
+
+
+def _pair_terms(x, eps=1.0, sigma=1.0):
+    p = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    n = len(p)
+    d = p[:, None, :] - p[None, :, :]
+    r2 = (d ** 2).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    s6 = (sigma * sigma / r2) ** 3
+    c = 24.0 * eps * (2 * s6 * s6 - s6) / r2
+    return p, n, d, s6, c
+
+
+def numpy_energy_grad(x, eps=1.0, sigma=1.0):
+    p, n, d, s6, c = _pair_terms(x, eps, sigma)
+    e = 2.0 * eps * (s6 * s6 - s6).sum()
+    g = -(c[:, :, None] * d).sum(1)
+    return float(e), g.reshape(-1)
+
+
+def grad_scale(x, eps=1.0, sigma=1.0):
+    p, n, d, s6, c = _pair_terms(x, eps, sigma)
+    return float(np.linalg.norm((np.abs(c)[:, :, None] * np.abs(d)).sum(1)))

@@ -1,0 +1,434 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated by the workload): the FP64 path within 1e-10 relative in
+energy; the mixed path within 1e-6 relative per evaluation and 1e-6 absolute in
+the final energy of minima both sides reach in the same basin (sorted
+pair-distance fingerprint within 1e-3 sigma).  Minimisation trajectories are
+chaotic, so different minima are both valid outcomes: they are compared where
+unique (same basin -> same energy) and otherwise checked for validity
+(FP64 gradient below gtol at the returned point, energy consistent with it).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_25938_gb300 import inputs as I
+from tests.helpers import fingerprint, grad_scale, numpy_energy_grad, same_basin
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_REL_E = 1e-10
+MIX_REL_E = 1e-6
+MIX_ABS_FINAL = 1e-6
+GTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lj():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_25938_gb300 import build
+    build.build()
+    from paper_2510_25938_gb300 import lj_bh
+    return lj_bh
+
+
+@pytest.fixture(scope="module")
+def ctx(lj):
+    c = lj.Ctx(0)
+    yield c
+    c.close()
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _uneven(sizes, seed, rho=0.3):
+    x, off = I.uneven_cube_starts(sizes, rho, seed)
+    return x, off
+
+
+def _oracle_minima(n_cand, n_atoms, side, seed):
+    x0 = I.cube_starts(n_cand, n_atoms, side, seed)
+    xm, em, st, _, _ = O.lbfgs_batch(x0, n_cand, uniform_n=n_atoms)
+    return xm.reshape(n_cand, -1), em, st
+
+
+# ---------------------------------------------------------------------------
+# lj_energy_grad_batched
+# ---------------------------------------------------------------------------
+def _eval_compare(lj, ctx, x, off, prec, xdtype, rel_e, rel_g):
+    n_cand = off.size - 1
+    sizes = np.diff(off)
+    xin = x.astype(np.float32).astype(np.float64) if xdtype == torch.float32 else x
+    e_ref, g_ref = O.eval_batch(xin, n_cand, atom_off=off)
+    xd = _cuda(xin, xdtype)
+    e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(xd)
+    lj.lj_energy_grad_batched(ctx, xd, e, g, n_cand=n_cand, atom_offset=_cuda(off, torch.int64),
+                              max_n=int(sizes.max()), prec=prec)
+    torch.cuda.synchronize()
+    e = e.cpu().numpy()
+    g = g.cpu().numpy().astype(np.float64)
+    for c in range(n_cand):
+        a0, a1 = 3 * off[c], 3 * off[c + 1]
+        if sizes[c] <= 1:
+            assert e[c] == 0.0 and np.all(g[a0:a1] == 0)
+            continue
+        assert abs(e[c] - e_ref[c]) <= rel_e * abs(e_ref[c]), (c, sizes[c], e[c], e_ref[c])
+        scale = max(np.linalg.norm(g_ref[a0:a1]), grad_scale(xin[a0:a1]))
+        assert np.linalg.norm(g[a0:a1] - g_ref[a0:a1]) <= rel_g * scale, (c, sizes[c])
+
+
+# sizes cross every team variant and leave ragged tails in each
+RAGGED_SIZES = [0, 1, 2, 3, 13, 31, 32, 33, 38, 63, 64, 65, 100, 127, 128, 129, 150, 255, 256,
+                257, 300, 511, 512, 513, 700]
+
+
+def test_eval_fp64_ragged(lj, ctx):
+    x, off = _uneven(RAGGED_SIZES, 11)
+    _eval_compare(lj, ctx, x, off, lj.LJ_PREC_FP64, torch.float64, FP64_REL_E, FP64_REL_E)
+
+
+def test_eval_fp32_ragged(lj, ctx):
+    x, off = _uneven(RAGGED_SIZES, 12)
+    _eval_compare(lj, ctx, x, off, lj.LJ_PREC_FP32, torch.float32, MIX_REL_E, MIX_REL_E)
+
+
+def test_eval_fp32_math_on_fp64_input(lj, ctx):
+    """FP64 input with FP32 arithmetic: the kernel rounds the coordinates to
+    FP32 and evaluates there; the reference is Eq. (1) at those coordinates."""
+    x, off = _uneven([13, 38, 38, 150], 13)
+    xr = x.astype(np.float32).astype(np.float64)
+    e_ref, g_ref = O.eval_batch(xr, 4, atom_off=off)
+    e = torch.empty(4, dtype=torch.float64, device="cuda")
+    g = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    lj.lj_energy_grad_batched(ctx, _cuda(x), e, g, n_cand=4, atom_offset=_cuda(off, torch.int64),
+                              max_n=150, prec=lj.LJ_PREC_FP32)
+    e = e.cpu().numpy()
+    g = g.cpu().numpy()
+    assert np.all(np.abs(e - e_ref) <= MIX_REL_E * np.abs(e_ref))
+    for c in range(4):
+        a0, a1 = 3 * off[c], 3 * off[c + 1]
+        scale = max(np.linalg.norm(g_ref[a0:a1]), grad_scale(xr[a0:a1]))
+        assert np.linalg.norm(g[a0:a1] - g_ref[a0:a1]) <= MIX_REL_E * scale
+
+
+@pytest.mark.parametrize("prec,xdt,rel", [(0, torch.float64, FP64_REL_E),
+                                          (1, torch.float32, MIX_REL_E)])
+def test_eval_jittered_minima_uniform_batch(lj, ctx, prec, xdt, rel):
+    """The evaluation workload at test scale: LJ38 local minima (oracle) with
+    Gaussian jitter 0.05 sigma, uniform batch layout."""
+    seeds, _, _ = _oracle_minima(16, 38, 3.2, I.workload_seed(2))
+    x = I.jitter(np.repeat(seeds, 8, axis=0), 0.05, I.workload_seed(2) + 1)
+    n_cand = x.shape[0]
+    xin = x.astype(np.float32).astype(np.float64) if xdt == torch.float32 else x
+    e_ref, g_ref = O.eval_batch(xin, n_cand, uniform_n=38)
+    xd = _cuda(xin, xdt)
+    e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(xd)
+    lj.lj_energy_grad_batched(ctx, xd, e, g, n_cand=n_cand, uniform_n=38, prec=prec)
+    e = e.cpu().numpy()
+    g = g.cpu().numpy().reshape(n_cand, -1).astype(np.float64)
+    rel_e = np.abs(e - e_ref) / np.abs(e_ref)
+    assert rel_e.max() <= rel
+    g_ref = g_ref.reshape(n_cand, -1)
+    for c in range(n_cand):
+        scale = max(np.linalg.norm(g_ref[c]), grad_scale(xin[c]))
+        assert np.linalg.norm(g[c] - g_ref[c]) <= rel * scale
+
+
+def test_eval_degenerate_inputs(lj, ctx):
+    # coincident atoms -> non-finite energy; oversize candidate -> NaN (bad input)
+    x = np.array([0, 0, 0, 0, 0, 0, 2, 0, 0] + [0, 0, 0, 1.2, 0, 0], dtype=np.float64)
+    off = np.array([0, 3, 5])
+    e = torch.empty(2, dtype=torch.float64, device="cuda")
+    lj.lj_energy_grad_batched(ctx, _cuda(x), e, None, n_cand=2,
+                              atom_offset=_cuda(off, torch.int64), max_n=3, prec=0)
+    e = e.cpu().numpy()
+    assert not np.isfinite(e[0])
+    assert e[1] == pytest.approx(4 * (1.2 ** -12 - 1.2 ** -6), rel=1e-14)
+    e2 = torch.empty(2, dtype=torch.float64, device="cuda")
+    lj.lj_energy_grad_batched(ctx, _cuda(x), e2, None, n_cand=2,
+                              atom_offset=_cuda(off, torch.int64), max_n=2, prec=0)
+    assert math.isnan(e2[0].item())
+    # empty batch: no launch, no error
+    lj.lj_energy_grad_batched(ctx, _cuda(x), e2, None, n_cand=0, uniform_n=3, prec=0)
+
+
+def test_eval_eps_sigma(lj, ctx):
+    x, off = _uneven([13, 38], 14)
+    e_ref, g_ref = O.eval_batch(x, 2, atom_off=off, eps=1.7, sigma=1.3)
+    e = torch.empty(2, dtype=torch.float64, device="cuda")
+    g = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    lj.lj_energy_grad_batched(ctx, _cuda(x), e, g, n_cand=2, atom_offset=_cuda(off, torch.int64),
+                              max_n=38, prec=0, eps=1.7, sigma=1.3)
+    assert np.allclose(e.cpu().numpy(), e_ref, rtol=1e-12)
+    assert np.allclose(g.cpu().numpy(), g_ref, rtol=1e-10, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# lbfgs_minimize_batched
+# ---------------------------------------------------------------------------
+def _minimise_gpu(lj, ctx, x, off=None, uniform_n=0, prec=0, **kw):
+    n_cand = (off.size - 1) if off is not None else x.shape[0]
+    xd = _cuda(x.reshape(-1))
+    e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+    st = torch.empty(n_cand, dtype=torch.int32, device="cuda")
+    it = torch.empty(n_cand, dtype=torch.int32, device="cuda")
+    ne = torch.empty(n_cand, dtype=torch.int32, device="cuda")
+    stats = lj.new_stats()
+    p = lj.LbfgsParams(prec=prec, **kw)
+    if off is not None:
+        lj.lbfgs_minimize_batched(ctx, xd, e, st, it, ne, stats, n_cand=n_cand,
+                                  atom_offset=_cuda(off, torch.int64),
+                                  max_n=int(np.diff(off).max()), params=p)
+    else:
+        lj.lbfgs_minimize_batched(ctx, xd, e, st, it, ne, stats, n_cand=n_cand,
+                                  uniform_n=uniform_n, params=p)
+    torch.cuda.synchronize()
+    return (xd.cpu().numpy(), e.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy(),
+            ne.cpu().numpy(), lj.stats_dict(stats))
+
+
+def _compare_minima(x0, off, xg, eg, sg, xo, eo, so, abs_tol, rel_tol, min_same):
+    n_cand = off.size - 1
+    n_same = n_both = 0
+    for c in range(n_cand):
+        a0, a1 = 3 * off[c], 3 * off[c + 1]
+        if a1 - a0 <= 3:
+            continue
+        e_chk, g_chk = numpy_energy_grad(xg[a0:a1])
+        if sg[c] == O.CONVERGED:
+            # valid local minimum: FP64 gradient below gtol, energy of x
+            assert np.abs(g_chk).max() < GTOL * 1.01, c
+        if np.isfinite(eg[c]):
+            assert abs(e_chk - eg[c]) <= 1e-9 * max(1.0, abs(eg[c])), c
+            e_start, _ = numpy_energy_grad(x0[a0:a1])
+            assert eg[c] <= e_start + 1e-9 * abs(e_start), c          # descent
+        if sg[c] == O.CONVERGED and so[c] == O.CONVERGED:
+            n_both += 1
+            if same_basin(xg[a0:a1], xo[a0:a1]):
+                n_same += 1
+                assert abs(eg[c] - eo[c]) <= max(abs_tol, rel_tol * abs(eo[c])), \
+                    (c, eg[c], eo[c])
+    frac = n_same / max(n_both, 1)
+    print(f"same-basin fraction {n_same}/{n_both} = {frac:.3f}")
+    assert frac >= min_same
+    return frac
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("n_atoms,side,cfg", [(13, 2.0, 0), (38, 3.2, 1)])
+def test_minimise_cube_starts(lj, ctx, prec, n_atoms, side, cfg):
+    n_cand = 48
+    x0 = I.cube_starts(n_cand, n_atoms, side, I.workload_seed(cfg) + 100)
+    off = np.arange(n_cand + 1) * n_atoms
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, uniform_n=n_atoms, prec=prec)
+    xo, eo, so, ito, neo = O.lbfgs_batch(x0, n_cand, uniform_n=n_atoms)
+    assert np.all(np.isin(sg, [O.CONVERGED, O.LINESEARCH_FAIL]))
+    assert (sg == O.CONVERGED).mean() >= 0.9
+    assert stats["minimisations"] == n_cand
+    assert stats["converged"] == int((sg == O.CONVERGED).sum())
+    if prec == 0:
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, 0.0, FP64_REL_E, 0.6)
+    else:
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL, 0.0, 0.4)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_minimise_bh_trial_moves_lj38(lj, ctx, prec):
+    """Trial moves of the paper's kind (perturbations of minima by +-0.4
+    sigma per coordinate): most land in the same basin on both sides."""
+    seeds, _, _ = _oracle_minima(12, 38, 3.2, I.workload_seed(1) + 7)
+    x0 = np.stack([O.perturb(seeds[w], 0.4, 99, k, 0, w) for w in range(12) for k in range(4)])
+    n_cand = x0.shape[0]
+    off = np.arange(n_cand + 1) * 38
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, uniform_n=38, prec=prec)
+    xo, eo, so, _, _ = O.lbfgs_batch(x0, n_cand, uniform_n=38)
+    if prec == 0:
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, 0.0, FP64_REL_E, 0.7)
+    else:
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL, 0.0, 0.5)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_minimise_uneven_ragged(lj, ctx, prec):
+    sizes = [0, 1, 2, 4, 13, 33, 38, 64, 65, 100, 129, 150]
+    x0, off = _uneven(sizes, 21)
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, off=off, prec=prec)
+    xo, eo, so, _, _ = O.lbfgs_batch(x0, len(sizes), atom_off=off)
+    for c, n in enumerate(sizes):
+        if n <= 1:
+            assert sg[c] == O.CONVERGED and eg[c] == 0.0 and it[c] == 0
+    for c, n, emin in [(2, 2, -1.0), (3, 4, -6.0)]:
+        assert eg[c] == pytest.approx(emin, abs=1e-10)
+    _compare_minima(x0, off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL if prec else 0.0,
+                    0.0 if prec else FP64_REL_E, 0.3)
+
+
+def test_minimise_is_deterministic(lj, ctx):
+    x0 = I.cube_starts(16, 38, 3.2, 5)
+    a = _minimise_gpu(lj, ctx, x0, uniform_n=38, prec=2)
+    b = _minimise_gpu(lj, ctx, x0, uniform_n=38, prec=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_minimise_statuses(lj, ctx):
+    x0 = I.cube_starts(4, 13, 2.0, 6).reshape(-1)
+    bad = x0.copy()
+    bad[3:6] = bad[0:3]                       # coincident atoms in candidate 0
+    bad[3 * 13 + 4] = np.nan                  # NaN coordinate in candidate 1
+    _, eg, sg, it, _, _ = _minimise_gpu(lj, ctx, bad.reshape(4, -1), uniform_n=13, prec=2)
+    assert sg[0] == O.NONFINITE and sg[1] == O.NONFINITE
+    assert np.all(sg[2:] == O.CONVERGED)
+    _, _, sg, it, _, _ = _minimise_gpu(lj, ctx, x0.reshape(4, -1), uniform_n=13, prec=0,
+                                       max_iter=3)
+    assert np.all(sg == O.MAXITER) and np.all(it == 3)
+    _, _, sg, it, _, _ = _minimise_gpu(lj, ctx, x0.reshape(4, -1), uniform_n=13, prec=2,
+                                       deadline_cycles=1)
+    assert np.all(sg == 4) and np.all(it == 1)           # LJ_CAND_TIMEOUT after one step
+
+
+# ---------------------------------------------------------------------------
+# bh_step_batched
+# ---------------------------------------------------------------------------
+def _gpu_state(lj, st):
+    return {k: _cuda(st[k], dt) for k, dt in lj.STATE_KEYS}
+
+
+def _bh_start(n_walkers, n_atoms, side, seed, step0=0.4):
+    x0 = I.cube_starts(n_walkers, n_atoms, side, seed)
+    xm, em, st, _, _ = O.lbfgs_batch(x0, n_walkers, uniform_n=n_atoms)
+    assert np.all(st == O.CONVERGED)
+    xm = xm.reshape(n_walkers, -1)
+    return {"x_cur": xm.copy(), "e_cur": em.copy(), "x_best": xm.copy(), "e_best": em.copy(),
+            "stepsize": np.full(n_walkers, step0), "win_accept": np.zeros(n_walkers, np.int32),
+            "n_accept": np.zeros(n_walkers, np.int32)}
+
+
+def test_bh_perturbation_is_bit_exact(lj, ctx):
+    st = _bh_start(3, 7, 2.0, 9)
+    st["e_cur"][:] = 1e300                    # every trial is accepted
+    st["e_best"][:] = 1e300
+    st["stepsize"][:] = [0.4, 0.25, 1.0]
+    gs = _gpu_state(lj, st)
+    for prec in (0, 2):
+        gs = _gpu_state(lj, st)
+        p = lj.BhParams(K=1, kT=1.0, seed=77, step0=123, n_steps=1, walker0=5,
+                        min=lj.LbfgsParams(prec=prec, max_iter=0))
+        lj.bh_step_batched(ctx, gs, p)
+        xg = gs["x_cur"].cpu().numpy()
+        for w in range(3):
+            ref = O.perturb(st["x_cur"][w], st["stepsize"][w], 77, 0, 123, 5 + w)
+            assert np.array_equal(xg[w], ref), (prec, w)
+
+
+def _bh_compare(lj, ctx, n_walkers, n_atoms, side, K, n_steps, prec, seed, min_strict):
+    st = _bh_start(n_walkers, n_atoms, side, seed)
+    st0 = {k: v.copy() for k, v in st.items()}       # the oracle updates st in place
+    gs = _gpu_state(lj, st)
+    p = lj.BhParams(K=K, kT=0.8, seed=seed, n_steps=n_steps, min=lj.LbfgsParams(prec=prec))
+    tr = lj.new_trace(n_steps, n_walkers, K)
+    lj.bh_step_batched(ctx, gs, p, tr)
+    torch.cuda.synchronize()
+    trg = {k: v.cpu().numpy() for k, v in tr.items()}
+    po = O.BhParamsPy(K=K, kT=0.8, seed=seed, n_steps=n_steps)
+    tro = O.bh_run(st, po)
+    rtol = FP64_REL_E if prec == 0 else 0.0
+    atol = 0.0 if prec == 0 else MIX_ABS_FINAL
+    strict = total = 0
+    for w in range(n_walkers):
+        for s in range(n_steps):
+            total += 1
+            eg, eo = trg["trial_e"][s, w], tro["trial_e"][s, w]
+            match = np.all(np.abs(eg - eo) <= np.maximum(atol, rtol * np.abs(eo)))
+            if not match:
+                break                           # trajectories legitimately part here
+            assert trg["accepted"][s, w] == tro["accepted"][s, w], (w, s)
+            assert trg["stepsize"][s, w] == tro["stepsize"][s, w], (w, s)
+            strict += 1
+        # the GPU trace is self-consistent everywhere
+        e_cur = st0["e_cur"][w]
+        step = st0["stepsize"][w]
+        win = 0
+        for s in range(n_steps):
+            assert trg["stepsize"][s, w] == step
+            te = trg["trial_e"][s, w]
+            k = int(np.argmin(te))
+            assert trg["best_trial_e"][s, w] == te[k]
+            u = O.stream_uniform(seed, 2, 0, 0, s, w)
+            de = te[k] - e_cur
+            acc = de <= 0 or u < math.exp(-de / 0.8)
+            assert bool(trg["accepted"][s, w]) == acc
+            if acc:
+                e_cur = te[k]
+                win += 1
+            if (s + 1) % 10 == 0:
+                step = step / 0.9 if win / 10 > 0.5 else step * 0.9
+                win = 0
+        assert gs["e_cur"][w].item() == e_cur
+    frac = strict / total
+    print(f"steps matching the oracle exactly (before any divergence): {strict}/{total}")
+    assert frac >= min_strict
+    e_best = gs["e_best"].cpu().numpy()
+    xb = gs["x_best"].cpu().numpy()
+    for w in range(n_walkers):
+        assert abs(numpy_energy_grad(xb[w])[0] - e_best[w]) <= 1e-9 * abs(e_best[w])
+    return frac
+
+
+def test_bh_lj13_fp64_matches_oracle(lj, ctx):
+    _bh_compare(lj, ctx, 4, 13, 2.0, 1, 40, 0, I.workload_seed(0), 0.7)
+
+
+def test_bh_lj13_mixed_matches_oracle(lj, ctx):
+    _bh_compare(lj, ctx, 4, 13, 2.0, 2, 30, 2, I.workload_seed(0) + 1, 0.4)
+
+
+def test_bh_lj38_k8_fp64(lj, ctx):
+    _bh_compare(lj, ctx, 4, 38, 3.2, 8, 4, 0, I.workload_seed(1), 0.4)
+
+
+def test_bh_lj38_k8_mixed(lj, ctx):
+    _bh_compare(lj, ctx, 4, 38, 3.2, 8, 4, 2, I.workload_seed(1) + 3, 0.2)
+
+
+# ---------------------------------------------------------------------------
+# argument validation (host-side; nothing reaches the GPU)
+# ---------------------------------------------------------------------------
+def test_invalid_arguments(lj, ctx):
+    x = torch.zeros(3 * 13 * 2, dtype=torch.float64, device="cuda")
+    e = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(lj.LjError) as ei:
+        lj.lbfgs_minimize_batched(ctx, x, e, n_cand=2, uniform_n=13,
+                                  params=lj.LbfgsParams(m=0))
+    assert ei.value.status == lj.LJ_ERR_INVALID_ARG
+    with pytest.raises(lj.LjError) as ei:
+        lj.lbfgs_minimize_batched(ctx, x, e, n_cand=2, uniform_n=2000)
+    assert ei.value.status == lj.LJ_ERR_UNSUPPORTED
+    with pytest.raises(lj.LjError) as ei:
+        lj.lbfgs_minimize_batched(ctx, x, e, n_cand=-1, uniform_n=13)
+    assert ei.value.status == lj.LJ_ERR_INVALID_ARG
+    with pytest.raises(lj.LjError) as ei:
+        lj.lj_energy_grad_batched(ctx, x, e, n_cand=2, uniform_n=13, eps=-1.0)
+    assert ei.value.status == lj.LJ_ERR_INVALID_ARG
+    st = {k: torch.zeros((2, 39) if k.startswith("x") else 2, dtype=dt, device="cuda")
+          for k, dt in lj.STATE_KEYS}
+    with pytest.raises(lj.LjError) as ei:
+        lj.bh_step_batched(ctx, st, lj.BhParams(K=0))
+    assert ei.value.status == lj.LJ_ERR_INVALID_ARG
+    with pytest.raises(lj.LjError) as ei:
+        lj.bh_step_batched(ctx, st, lj.BhParams(K=32))          # 32 warps > 256 threads
+    assert ei.value.status == lj.LJ_ERR_UNSUPPORTED
+    # misaligned device pointer, through the raw C entry point
+    import ctypes as C
+    lib = lj.load()
+    b = lj._Batch(2, 13, None, 13)
+    rc = lib.lj_energy_grad_batched(ctx.handle, C.byref(b), 0, lj.LJ_F64, x.data_ptr() + 4,
+                                    e.data_ptr(), None, 1.0, 1.0, None)
+    assert rc == lj.LJ_ERR_INVALID_ARG
