@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="mixed-precision steps only (no FP64 arm, e2e or CPU legs): the "
+                         "command to run under ncu; numbers printed then are not bench values")
     return ap.parse_args()
 
 
@@ -73,10 +76,10 @@ def flops_from_stats(s):
     """Algorithmic flops: 28 per unordered pair per evaluation, and per
     L-BFGS iteration 8 * (history pairs used) * 3N (two dots + two axpys per
     pair) + 12 * 3N for the remaining vector updates."""
-    pair = 28.0 * (s["pairs32"] + s["pairs64"])
+    pair = 28.0 * (s["pairs32"] + s["pairs64"] + s["pairs_df"])
     vec = 8.0 * (s["vec_elems32"] + s["vec_elems64"]) + 12.0 * 3 * N_ATOMS * (
         s["iters32"] + s["iters64"])
-    return pair + vec, 28.0 * s["pairs64"]
+    return pair + vec, 28.0 * (s["pairs64"] + s["pairs_df"])
 
 
 class ClockSampler:
@@ -302,6 +305,12 @@ def run_cuda(args):
     value = conv / t_dev
     flops, flops64 = flops_from_stats(st_mix)
     achieved_tf = flops / t_dev / 1e12 if world == 1 else None
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "steps": args.steps, "ms_per_step":
+                              1e3 * t_dev / args.steps, "work": st_mix}), flush=True)
+        ctx.close()
+        return 0
     # ---- FP64 path on the same workload --------------------------------------
     n64 = args.fp64_steps if args.fp64_steps is not None else max(3, args.steps // 8)
     t64, _, st64, _, _ = timed_run(L.LJ_PREC_FP64, n64, min(args.warmup, 3))
@@ -340,7 +349,7 @@ def run_cuda(args):
                       "mixed_over_fp64": value / value64 if value64 > 0 else None,
                       "achieved_tflops": flops_64path / t64 / 1e12,
                       "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
-        "work": {k: st_mix[k] for k in ("evals32", "evals64", "iters32", "iters64")},
+        "work": {k: st_mix[k] for k in ("evals32", "evals64", "evals_df", "iters32", "iters64")},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,
@@ -348,7 +357,7 @@ def run_cuda(args):
     if achieved_tf is not None:
         line["roofline"] = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                            "traffic": None, "kernel": "bh_kernel<32,2,mixed>",
+                            "traffic": None, "kernel": "bh_cluster_kernel<32,2,mixed>",
                             "fp64_flop_share": flops64 / flops if flops else None}
     if e2e:
         line["e2e"] = e2e

@@ -66,10 +66,12 @@ typedef enum { LJ_F32 = 0, LJ_F64 = 1 } lj_dtype;
 typedef enum {
     LJ_PREC_FP64 = 0,   /* every operation in FP64 */
     LJ_PREC_FP32 = 1,   /* evaluation only: FP32 pair terms, compensated energy */
-    LJ_PREC_MIXED = 2   /* minimisation: FP32 phase, then FP64 polish whose
-                           evaluations (x, gradient, energy) are FP64 and whose
-                           search directions stay FP32; the convergence test
-                           and returned energy are FP64 */
+    LJ_PREC_MIXED = 2   /* minimisation: an FP32 phase, then a polish phase
+                           that carries x, gradient and energy in FP64 with
+                           pair terms in double-float arithmetic (FP32 pipes,
+                           ~1e-14 relative) and FP32 search directions; the
+                           convergence test and the returned energy come from
+                           a true FP64 evaluation */
 } lj_precision;
 
 /* per-candidate outcome, written by the device */
@@ -85,7 +87,7 @@ typedef enum {
 /* Library limits of this build. */
 #define LJ_MAX_ATOMS 1024        /* atoms per candidate */
 #define LJ_MAX_M 32              /* L-BFGS history length */
-#define LJ_MAX_K 32              /* candidates per walker and step */
+#define LJ_MAX_K 16              /* candidates per walker and step */
 
 typedef struct {
     int64_t n_cand;                /* number of candidates (>= 0) */
@@ -151,10 +153,12 @@ typedef struct {
 typedef struct {
     unsigned long long evals32;     /* FP32 energy+gradient evaluations */
     unsigned long long evals64;     /* FP64 energy+gradient evaluations */
+    unsigned long long evals_df;    /* double-float evaluations (mixed polish) */
     unsigned long long iters32;     /* L-BFGS iterations in the FP32 phase */
     unsigned long long iters64;     /* L-BFGS iterations in FP64 / polish */
     unsigned long long pairs32;     /* unordered atom pairs evaluated in FP32 */
     unsigned long long pairs64;     /* unordered atom pairs evaluated in FP64 */
+    unsigned long long pairs_df;    /* unordered atom pairs evaluated in double-float */
     unsigned long long vec_elems32; /* sum over iterations of m_used * 3N (FP32 vectors) */
     unsigned long long vec_elems64; /* same for FP64 vectors */
     unsigned long long converged;   /* candidates with LJ_CAND_CONVERGED */

@@ -298,7 +298,7 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   cudaError_t e = ljh::bh_plan(s->n_atoms, p->min.m, mixed, s->n_walkers, p->K, &plan);
   if (e == cudaErrorNotSupported)
     return fail(ctx, LJ_ERR_UNSUPPORTED,
-                "bh_step_batched supports K * team_size <= 256 and N <= 256 in this build");
+                "bh_step_batched supports clusters of up to 256 atoms in this build");
   if (e != cudaSuccess) return cuda_fail(ctx, e, "bh_step_batched plan");
   st = ensure_ws(ctx, (size_t)plan.slots * plan.slot_bytes);
   if (st != LJ_OK) return st;

@@ -10,11 +10,19 @@
 //   4. Metropolis: accept if dE <= 0 or u < exp(-dE / kT), u from stream 2;
 //   5. adaptation: after every step s with (s+1) % interval == 0 the window
 //      acceptance rate moves the step size (up if above target, else down).
-// The walker's x_cur and x_best live in shared memory for all n_steps; the
-// winning team copies its registers into x_cur on acceptance.
+// Layout: one thread-block cluster per walker and one CTA (one team) per
+// candidate (K <= 16), so the W*K candidates spread over every SM.  Each CTA
+// keeps a replica of the walker state (x_cur, x_best, scalars) in shared
+// memory for all n_steps; after the minimisations the CTAs read each other's
+// energies and the winner's coordinates through distributed shared memory,
+// and every CTA takes the same (deterministic) decision.
+#include <cooperative_groups.h>
+
 #include "lj_internal.h"
 #include "lj_minimize.cuh"
 #include "lj_teams.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -35,33 +43,35 @@ struct BhShared {          // walker scalars, owned by thread 0 between barriers
 };
 
 template <int T>
-__host__ __device__ constexpr size_t bh_head_bytes(int n_atoms, int K) {
-  return align16(sizeof(BhShared)) + align16((size_t)K * sizeof(double)) +
-         2 * align16((size_t)3 * n_atoms * sizeof(double));
+__host__ __device__ constexpr size_t bhc_head_bytes(int n_atoms) {
+  return align16(sizeof(BhShared)) + 16 + 3 * align16((size_t)3 * n_atoms * sizeof(double));
 }
 
 template <int T, int A, bool MIXED>
-__global__ void __launch_bounds__(256) bh_kernel(ljh::BhArgs a) {
+__global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
   const int n = a.n_atoms;
   const int K = a.K;
-  const int w = blockIdx.x;
-  const int k = threadIdx.x / T;
+  const int k = (int)cl.block_rank();
+  const int w = blockIdx.x / K;
   Team<T> tm;
-  tm.rank = threadIdx.x % T;
-  tm.bar = k + 1;
+  tm.rank = threadIdx.x;
+  tm.bar = 1;
   unsigned char* sp = smem;
   BhShared* sh = reinterpret_cast<BhShared*>(sp);
   sp += align16(sizeof(BhShared));
-  double* ek = reinterpret_cast<double*>(sp);
-  sp += align16((size_t)K * sizeof(double));
+  double* my_e = reinterpret_cast<double*>(sp);       // this candidate's energy
+  sp += 16;
+  double* xmine = reinterpret_cast<double*>(sp);      // this candidate's minimum
+  sp += align16((size_t)3 * n * sizeof(double));
   double* xcur = reinterpret_cast<double*>(sp);
   sp += align16((size_t)3 * n * sizeof(double));
   double* xbest = reinterpret_cast<double*>(sp);
   sp += align16((size_t)3 * n * sizeof(double));
   void* pos;
   long long* word;
-  carve_team<T>(sp + k * team_smem_bytes<T>(n), n, pos, tm.red, word);
+  carve_team<T>(sp, n, pos, tm.red, word);
   const MinParams p = to_dev(a.p);
   void* hist = static_cast<unsigned char*>(a.hist) + ((size_t)w * K + k) * a.hist_slot_bytes;
   const uint32_t wg = (uint32_t)(a.walker0 + w);
@@ -84,7 +94,6 @@ __global__ void __launch_bounds__(256) bh_kernel(ljh::BhArgs a) {
     const long long s64 = a.step0 + it;
     const uint32_t s = (uint32_t)s64;
     const double step = sh->step;
-    // 1. perturbation of the atoms this thread owns
     double x64[A][3];
 #pragma unroll
     for (int sl = 0; sl < A; ++sl) {
@@ -101,11 +110,18 @@ __global__ void __launch_bounds__(256) bh_kernel(ljh::BhArgs a) {
         }
       }
     }
-    // 2. local minimisation
     MinResult r;
     minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, r);
+#pragma unroll
+    for (int sl = 0; sl < A; ++sl) {
+      const int i = tm.rank + sl * T;
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xmine[3 * i + c] = x64[sl][c];
+      }
+    }
     if (tm.rank == 0) {
-      ek[k] = r.E;
+      *my_e = r.E;
       const size_t tix = ((size_t)it * a.n_walkers + w) * K + k;
       if (a.tr.trial_e) a.tr.trial_e[tix] = r.E;
       if (a.tr.trial_status) a.tr.trial_status[tix] = r.status;
@@ -114,36 +130,40 @@ __global__ void __launch_bounds__(256) bh_kernel(ljh::BhArgs a) {
         const unsigned long long np = (unsigned long long)n * (unsigned long long)(n - 1) / 2;
         atomicAdd(&a.stats->evals32, (unsigned long long)r.evals32);
         atomicAdd(&a.stats->evals64, (unsigned long long)r.evals64);
+        atomicAdd(&a.stats->evals_df, (unsigned long long)r.evals_df);
         atomicAdd(&a.stats->iters32, (unsigned long long)r.iters32);
         atomicAdd(&a.stats->iters64, (unsigned long long)r.iters64);
         atomicAdd(&a.stats->pairs32, np * (unsigned long long)r.evals32);
         atomicAdd(&a.stats->pairs64, np * (unsigned long long)r.evals64);
+        atomicAdd(&a.stats->pairs_df, np * (unsigned long long)r.evals_df);
         atomicAdd(&a.stats->vec_elems32, (unsigned long long)r.vec32);
         atomicAdd(&a.stats->vec_elems64, (unsigned long long)r.vec64);
         atomicAdd(&a.stats->converged, r.status == ST_CONVERGED ? 1ULL : 0ULL);
         atomicAdd(&a.stats->minimisations, 1ULL);
       }
     }
-    __syncthreads();
-    // 3-5. selection, Metropolis, adaptation (one thread)
+    cl.sync();   // every candidate's energy and minimum are visible cluster-wide
     if (threadIdx.x == 0) {
       int kb = -1;
+      double eb = 0.0;
       for (int kk = 0; kk < K; ++kk) {
-        const double e = ek[kk];
-        if (isfinite(e) && (kb < 0 || e < ek[kb])) kb = kk;
+        const double e = *cl.map_shared_rank(my_e, kk);
+        if (isfinite(e) && (kb < 0 || e < eb)) { kb = kk; eb = e; }
       }
       int acc = 0, better = 0;
       double e_sel = __longlong_as_double(0x7ff0000000000000LL);
       if (kb >= 0) {
-        e_sel = ek[kb];
+        e_sel = eb;
         const double u = stream_u01(a.seed, 2u, 0u, 0u, s, wg);
         const double de = e_sel - sh->e_cur;
         acc = (de <= 0.0) || (u < exp(-de / a.kT));
       }
-      const size_t tw = (size_t)it * a.n_walkers + w;
-      if (a.tr.best_trial_e) a.tr.best_trial_e[tw] = e_sel;
-      if (a.tr.accepted) a.tr.accepted[tw] = (uint8_t)acc;
-      if (a.tr.stepsize) a.tr.stepsize[tw] = step;
+      if (k == 0) {
+        const size_t tw = (size_t)it * a.n_walkers + w;
+        if (a.tr.best_trial_e) a.tr.best_trial_e[tw] = e_sel;
+        if (a.tr.accepted) a.tr.accepted[tw] = (uint8_t)acc;
+        if (a.tr.stepsize) a.tr.stepsize[tw] = step;
+      }
       if (acc) {
         sh->e_cur = e_sel;
         sh->nacc += 1;
@@ -163,60 +183,85 @@ __global__ void __launch_bounds__(256) bh_kernel(ljh::BhArgs a) {
       sh->better = better;
     }
     __syncthreads();
-    if (sh->acc && k == sh->kbest) {
-#pragma unroll
-      for (int sl = 0; sl < A; ++sl) {
-        const int i = tm.rank + sl * T;
-        if (i < n) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            xcur[3 * i + c] = x64[sl][c];
-            if (sh->better) xbest[3 * i + c] = x64[sl][c];
-          }
-        }
+    if (sh->acc) {
+      const double* xw = cl.map_shared_rank(xmine, sh->kbest);
+      for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+        const double v = xw[q];
+        xcur[q] = v;
+        if (sh->better) xbest[q] = v;
       }
     }
-    __syncthreads();
+    cl.sync();   // nobody overwrites its energy / minimum while others read them
   }
-  for (int q = threadIdx.x; q < n3; q += blockDim.x) {
-    a.x_cur[(size_t)w * n3 + q] = xcur[q];
-    a.x_best[(size_t)w * n3 + q] = xbest[q];
-  }
-  if (threadIdx.x == 0) {
-    a.e_cur[w] = sh->e_cur;
-    a.e_best[w] = sh->e_best;
-    a.stepsize[w] = sh->step;
-    a.win_accept[w] = sh->win;
-    a.n_accept[w] = sh->nacc;
+  if (k == 0) {
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+      a.x_cur[(size_t)w * n3 + q] = xcur[q];
+      a.x_best[(size_t)w * n3 + q] = xbest[q];
+    }
+    if (threadIdx.x == 0) {
+      a.e_cur[w] = sh->e_cur;
+      a.e_best[w] = sh->e_best;
+      a.stepsize[w] = sh->step;
+      a.win_accept[w] = sh->win;
+      a.n_accept[w] = sh->nacc;
+    }
   }
 }
 
 template <int T, int A, bool MIXED>
 cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out) {
-  if (K * T > 256) return cudaErrorNotSupported;
-  const size_t smem = bh_head_bytes<T>(n_atoms, K) + (size_t)K * team_smem_bytes<T>(n_atoms);
-  auto k = bh_kernel<T, A, MIXED>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  out->team = T;
-  out->teams_per_cta = K;
-  out->grid = n_walkers;
-  out->smem = smem;
-  out->slots = (int64_t)n_walkers * K;
   out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
-  return cudaSuccess;
+  out->slots = (int64_t)n_walkers * K;
+  out->team = T;
+  if (K <= LJ_MAX_K) {                // one cluster of K CTAs per walker
+    const size_t smem = bhc_head_bytes<T>(n_atoms) + team_smem_bytes<T>(n_atoms);
+    auto k = bh_cluster_kernel<T, A, MIXED>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (K > 8) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    out->teams_per_cta = 1;
+    out->grid = n_walkers * K;
+    out->smem = smem;
+    out->cluster = K;
+    return cudaSuccess;
+  }
+  return cudaErrorNotSupported;
+}
+
+template <int T, int A, bool MIXED>
+cudaError_t launch_cluster(const ljh::BhArgs& a, const ljh::Plan& plan, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)plan.grid, 1, 1);
+  cfg.blockDim = dim3(T, 1, 1);
+  cfg.dynamicSmemBytes = plan.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)plan.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bh_cluster_kernel<T, A, MIXED>, a);
 }
 
 }  // namespace
 
 namespace ljh {
 
-// Basin Hopping keeps a walker's K teams in one CTA, so it supports the team
-// sizes up to 256 atoms per cluster.
+// Basin Hopping runs one candidate per CTA with the team sizes up to 128
+// threads (clusters of up to 256 atoms).
 template <class F>
 static cudaError_t dispatch_bh(int n, F&& f) {
-  if (n > 256) return cudaErrorNotSupported;
-  return dispatch_team(n, f);
+  using std::integral_constant;
+  if (n <= 32) return f(integral_constant<int, 32>{}, integral_constant<int, 1>{});
+  if (n <= 64) return f(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+  if (n <= 128) return f(integral_constant<int, 64>{}, integral_constant<int, 2>{});
+  if (n <= 256) return f(integral_constant<int, 128>{}, integral_constant<int, 2>{});
+  return cudaErrorNotSupported;
 }
 
 cudaError_t bh_plan(int n_atoms, int m, int mixed, int n_walkers, int K, Plan* out) {
@@ -232,12 +277,9 @@ cudaError_t bh_launch(const BhArgs& a, const Plan& plan, cudaStream_t s) {
   return dispatch_bh(a.n_atoms, [&](auto TT, auto AA) -> cudaError_t {
     constexpr int T = decltype(TT)::value;
     constexpr int A = decltype(AA)::value;
-    const int threads = a.K * T;
-    if (a.mixed) {
-      bh_kernel<T, A, true><<<plan.grid, threads, plan.smem, s>>>(a);
-    } else {
-      bh_kernel<T, A, false><<<plan.grid, threads, plan.smem, s>>>(a);
-    }
+    cudaError_t e = a.mixed ? launch_cluster<T, A, true>(a, plan, s)
+                            : launch_cluster<T, A, false>(a, plan, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   });
 }

@@ -362,4 +362,86 @@ __device__ __forceinline__ void pair_row_f64(int n, int i, double px, double py,
   e.lo = __dadd_rn(e.lo, s.lo);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float ("df") arithmetic: a value is hi + lo with two FP32 words
+// (~48-bit significand), built from error-free transformations on the FP32
+// pipes (TwoSum, and TwoProd via FMA; Dekker 1971, Knuth TAOCP 4.2.2).  The
+// mixed path evaluates its polish phase with these: on GB300 one FP64
+// instruction issues at ~1/62 the FP32 rate, so ~200 FP32 operations per pair
+// cost several times less than ~27 FP64 ones while giving ~1e-14 relative
+// accuracy.  Products whose rounded value enters an error term use the _rn
+// intrinsics so that no multiply is contracted into a later add.
+// ---------------------------------------------------------------------------
+struct alignas(16) PosDF { float xh, yh, zh, wh, xl, yl, zl, wl; };
+
+__device__ __forceinline__ ff df_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return ff{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff df_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff df_sub(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, -b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff df_add_f(ff a, float b) {
+  const ff s = ff_two_sum(a.hi, b);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff df_mul(ff a, ff b) {
+  const ff p = df_two_prod(a.hi, b.hi);
+  const float e = fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, p.lo));
+  return df_fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ ff df_sqr(ff a) {
+  const ff p = df_two_prod(a.hi, a.hi);
+  return df_fast_two_sum(p.hi, fmaf(__fmul_rn(2.f, a.hi), a.lo, p.lo));
+}
+// 1 / a: FP32 reciprocal estimate refined by one Newton step in df,
+// w = r + r (1 - a r); relative error ~ (rel. error of r)^2 + 2^-47
+__device__ __forceinline__ ff df_rcp(ff a) {
+  const float r = rcp_approx(a.hi);
+  const ff p = df_two_prod(a.hi, r);
+  float t = __fsub_rn(__fsub_rn(1.f, p.hi), p.lo);
+  t = fmaf(-a.lo, r, t);
+  return df_fast_two_sum(r, __fmul_rn(r, t));
+}
+__device__ __forceinline__ ff df_from_double(double x) {
+  const float h = (float)x;
+  return ff{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// One row of the pair sum in df arithmetic, coordinates pre-scaled by
+// 1/sigma (so s2 = 1/r^2).  Accumulates acc_i = sum_j s2 s6 (2 s6 - 1) d_ij
+// and e_i = sum_j s6 (s6 - 1), both as df.
+__device__ __forceinline__ void pair_row_df(int n, int i, ff px, ff py, ff pz,
+                                            const PosDF* __restrict__ pos,
+                                            ff& ax, ff& ay, ff& az, ff& e) {
+  ax = ff{0.f, 0.f}; ay = ff{0.f, 0.f}; az = ff{0.f, 0.f};
+#pragma unroll 2
+  for (int j = 0; j < n; ++j) {
+    const PosDF q = pos[j];
+    const ff dx = df_sub(px, ff{q.xh, q.xl});
+    const ff dy = df_sub(py, ff{q.yh, q.yl});
+    const ff dz = df_sub(pz, ff{q.zh, q.zl});
+    const ff r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+    ff s2 = df_rcp(r2);
+    if (j == i) s2 = ff{0.f, 0.f};
+    const ff s6 = df_mul(df_sqr(s2), s2);
+    const ff t = df_add_f(s6, -1.f);
+    e = df_add(e, df_mul(s6, t));
+    const ff c = df_mul(df_mul(s2, s6), df_add(s6, t));
+    ax = df_add(ax, df_mul(c, dx));
+    ay = df_add(ay, df_mul(c, dy));
+    az = df_add(az, df_mul(c, dz));
+  }
+}
+
 }  // namespace ljd

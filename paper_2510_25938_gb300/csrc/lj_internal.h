@@ -74,6 +74,7 @@ struct Plan {
   size_t smem;       // dynamic shared memory per CTA
   int64_t slots;     // history slots the launch needs
   size_t slot_bytes; // bytes per history slot
+  int cluster = 1;   // CTAs per thread-block cluster (Basin Hopping: K)
 };
 
 // largest atom count this build supports

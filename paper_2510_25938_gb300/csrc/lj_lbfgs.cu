@@ -87,15 +87,17 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
       a.energy[c] = r.E;
       if (a.status) a.status[c] = r.status;
       if (a.iters) a.iters[c] = r.iters;
-      if (a.nevals) a.nevals[c] = r.evals32 + r.evals64;
+      if (a.nevals) a.nevals[c] = r.evals32 + r.evals64 + r.evals_df;
       if (a.stats) {
         const unsigned long long np = (unsigned long long)n * (unsigned long long)(n > 0 ? n - 1 : 0) / 2;
         atomicAdd(&a.stats->evals32, (unsigned long long)r.evals32);
         atomicAdd(&a.stats->evals64, (unsigned long long)r.evals64);
+        atomicAdd(&a.stats->evals_df, (unsigned long long)r.evals_df);
         atomicAdd(&a.stats->iters32, (unsigned long long)r.iters32);
         atomicAdd(&a.stats->iters64, (unsigned long long)r.iters64);
         atomicAdd(&a.stats->pairs32, np * (unsigned long long)r.evals32);
         atomicAdd(&a.stats->pairs64, np * (unsigned long long)r.evals64);
+        atomicAdd(&a.stats->pairs_df, np * (unsigned long long)r.evals_df);
         atomicAdd(&a.stats->vec_elems32, (unsigned long long)r.vec32);
         atomicAdd(&a.stats->vec_elems64, (unsigned long long)r.vec64);
         atomicAdd(&a.stats->converged, r.status == ST_CONVERGED ? 1ULL : 0ULL);

@@ -22,9 +22,13 @@
 //               FP64 instruction at all; it ends when ||g32||_inf <
 //               switch_gtol, when the predicted decrease falls below the FP32
 //               energy resolution, or when its line search fails.
-//               phase 2 (polish): coordinates, gradient and energy in FP64
-//               (FP64 pair terms); directions and history stay FP32 (they
-//               only steer); the stopping test uses the FP64 gradient.
+//               phase 2 (polish): coordinates, gradient and energy carried
+//               in FP64, pair terms in double-float arithmetic (FP32 pipes,
+//               ~1e-14 relative); directions and history stay FP32 (they only
+//               steer).  It hands over once the predicted decrease falls
+//               below the double-float energy resolution (~256 * 2^-48 |E|).
+//               phase 3: FP64 pair terms for the last iterations; the
+//               convergence test and the returned energy are always FP64.
 #pragma once
 #include "lj_device.cuh"
 #include "../../include/lj_bh.h"
@@ -42,7 +46,7 @@ struct MinResult {
   double E;
   int status;
   int iters;
-  int evals32, evals64, iters32, iters64;
+  int evals32, evals64, evals_df, iters32, iters64;
   long long vec32, vec64;   // sum over iterations of (history used) * 3N
 };
 
@@ -68,9 +72,11 @@ __device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
 // ---------------------------------------------------------------------------
 // Energy and gradient at x (owned atoms), and dphi = g . d when d != nullptr.
 // ---------------------------------------------------------------------------
-template <int T, int A, typename X, typename V>
+// PM = 0: pair terms in X precision; PM = 1 (X = double only): pair terms in
+// double-float arithmetic on coordinates scaled by 1/sigma.
+template <int T, int A, typename X, typename V, int PM = 0>
 __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[A][3], X (&g)[A][3],
-                                         typename PosOf<X>::type* pos, const MinParams& p,
+                                         void* posv, const MinParams& p,
                                          const V (*d)[3], typename Tr<X>::F& E,
                                          typename Tr<X>::S& dphi) {
   using S = typename Tr<X>::S;
@@ -81,14 +87,44 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
   for (int a = 0; a < A; ++a) {
     const int i = tm.rank + a * T;
     if (i < n) {
-      typename PosOf<X>::type q;
-      q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
-      pos[i] = q;
+      if constexpr (PM == 1) {
+        const double is = 1.0 / p.sigma;
+        const ff qx = df_from_double(x[a][0] * is), qy = df_from_double(x[a][1] * is),
+                 qz = df_from_double(x[a][2] * is);
+        static_cast<PosDF*>(posv)[i] = PosDF{qx.hi, qy.hi, qz.hi, 0.f, qx.lo, qy.lo, qz.lo, 0.f};
+      } else {
+        typename PosOf<X>::type q;
+        q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
+        static_cast<typename PosOf<X>::type*>(posv)[i] = q;
+      }
     }
   }
   tm.sync();
   V dp = (V)0;
-  if constexpr (sizeof(X) == 4) {
+  if constexpr (PM == 1) {
+    static_assert(sizeof(X) == 8, "double-float pairs work on FP64 coordinates");
+    const PosDF* pos = static_cast<const PosDF*>(posv);
+    const double gs = 24.0 * p.eps / p.sigma;
+    dd e{0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int i = tm.rank + a * T;
+      if (i < n) {
+        const PosDF q = pos[i];
+        ff ax, ay, az, ea{0.f, 0.f};
+        pair_row_df(n, i, ff{q.xh, q.xl}, ff{q.yh, q.yl}, ff{q.zh, q.zl}, pos, ax, ay, az, ea);
+        g[a][0] = -gs * df_to_double(ax);
+        g[a][1] = -gs * df_to_double(ay);
+        g[a][2] = -gs * df_to_double(az);
+        e = dd_add(e, dd_two_sum((double)ea.hi, (double)ea.lo));
+      } else {
+        g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    E = team_sum_dd<T>(tm, e) * (2.0 * p.eps);
+  } else if constexpr (sizeof(X) == 4) {
+    const PosF* pos = static_cast<const PosF*>(posv);
     ff e{0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
@@ -107,6 +143,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
     ff et = team_sum_ff<T>(tm, e);
     E = ff_scale(et, (float)(2.0 * p.eps));
   } else {
+    const PosD* pos = static_cast<const PosD*>(posv);
     dd e{0.0, 0.0};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
@@ -137,6 +174,17 @@ __device__ __forceinline__ X grad_max(const Team<T>& tm, const X (&g)[A][3]) {
   return v[0];
 }
 
+// Sufficient decrease f(a) <= f(0) + c1 a phi'(0).  FP64-valued energies use
+// exactly that expression (the right side rounded to FP64, as the oracle does:
+// near the FP64 floor a threshold below half an ulp of f(0) then asks only
+// f(a) <= f(0)); float-float energies compare the exact difference.
+__device__ __forceinline__ bool armijo_ok(double fa, double f0, double t) {
+  return isfinite(fa) && fa <= f0 + t;
+}
+__device__ __forceinline__ bool armijo_ok(ff fa, ff f0, float t) {
+  return fisfinite(fa) && fdiff(fa, f0) <= t;
+}
+
 // safeguarded cubic interpolation (N&W eq. 3.59), kept 10% inside the bracket
 template <typename S, typename F>
 __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
@@ -163,20 +211,30 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 
 // ---------------------------------------------------------------------------
 // One L-BFGS phase: iterate from (x, g, f) until a stop condition.
-// X: coordinates/gradient precision, V: direction/history precision.
-// F32PHASE: the mixed path's FP32 phase (never declares convergence).
+// X: coordinates/gradient precision, V: direction/history precision,
+// PM: pair arithmetic (0 native X, 1 double-float).
+// MODE 0 (FP64, final): stops on ||g||_inf < gtol (CONVERGED) or a failed
+//   line search (LSFAIL).
+// MODE 1 (mixed, FP32 phase): hands over (SWITCH) once ||g||_inf <
+//   switch_gtol, once the predicted decrease -alpha phi'(0) is below ~8 ulp
+//   of the FP32 energy, or when a line search fails; never converges.
+// MODE 2 (mixed, double-float polish): CONVERGED on ||g||_inf < gtol (to be
+//   confirmed in FP64); hands over to FP64 once the predicted decrease is
+//   below the double-float energy resolution, or when a line search fails.
 // ---------------------------------------------------------------------------
-template <int T, int A, typename X, typename V, bool F32PHASE>
+constexpr double kDfResolution = 256.0 * 3.552713678800501e-15;  // 256 * 2^-48, relative to |E|
+
+template <int T, int A, typename X, typename V, int MODE, int PM = 0>
 __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
                          typename Tr<X>::F& f, V* __restrict__ Sh, V* __restrict__ Yh,
                          V (&sy)[LJ_MAX_M], V (&yy)[LJ_MAX_M], int& cnt, int& head, int& iters,
-                         int& evals, int& phase_iters, long long& vec, typename PosOf<X>::type* pos,
+                         int& evals, int& phase_iters, long long& vec, void* pos,
                          const MinParams& p, long long t0) {
   using S = typename Tr<X>::S;
   using F = typename Tr<X>::F;
   const int m = p.m;
   const S c1 = (S)p.c1, c2 = (S)p.c2, amax = (S)p.alpha_max;
-  const X stop_gtol = F32PHASE ? (X)p.switch_gtol : (X)p.gtol;
+  const X stop_gtol = MODE == 1 ? (X)p.switch_gtol : (X)p.gtol;
   V alpha[LJ_MAX_M];
   V d[A][3];
   X xt[A][3], gt[A][3];
@@ -274,9 +332,12 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         a1 = (S)1 / S_sqrt(-dphi0);
         if (a1 > (S)1) a1 = (S)1;
       }
-      if constexpr (F32PHASE) {
-        // predicted decrease below ~8 ulp of the FP32 energy: hand over to FP64
+      if constexpr (MODE == 1) {
+        // predicted decrease below ~8 ulp of the FP32 energy: hand over
         if (-dphi0 * a1 < (S)4.76837158203125e-7 * fabsf(f.hi)) return PH_SWITCH;
+      } else if constexpr (MODE == 2) {
+        // predicted decrease below the double-float energy resolution
+        if (-dphi0 * a1 < (S)kDfResolution * fabs(f)) return PH_SWITCH;
       }
       // ---- strong-Wolfe line search ----------------------------------------
       int ev = 0;
@@ -295,7 +356,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         for (int aa = 0; aa < A; ++aa)
 #pragma unroll
           for (int c = 0; c < 3; ++c) xt[aa][c] = x[aa][c] + (X)al * (X)d[aa][c];
-        evaluate<T, A, X, V>(tm, n, xt, gt, pos, p, d, fo, dpo);
+        evaluate<T, A, X, V, PM>(tm, n, xt, gt, pos, p, d, fo, dpo);
         ++ev;
         last_a = al;
       };
@@ -303,7 +364,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         if (ev >= p.max_ls) break;
         F fa;
         trial(a, fa, dp);
-        const bool armijo = fisfinite(fa) && ((S)fdiff(fa, f) <= c1 * a * dphi0);
+        const bool armijo = armijo_ok(fa, f, c1 * a * dphi0);
         if (armijo && (!have_best || (S)fdiff(fa, best_f) < (S)0)) {
           have_best = true; best_f = fa; best_a = a;
         }
@@ -328,7 +389,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         const S aj = cubic_step<S, F>(lo, f_lo, dp_lo, hi, f_hi, dp_hi);
         F fa;
         trial(aj, fa, dp);
-        const bool armijo = fisfinite(fa) && ((S)fdiff(fa, f) <= c1 * aj * dphi0);
+        const bool armijo = armijo_ok(fa, f, c1 * aj * dphi0);
         if (armijo && (!have_best || (S)fdiff(fa, best_f) < (S)0)) {
           have_best = true; best_f = fa; best_a = aj;
         }
@@ -358,7 +419,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
       evals += ev;
       ok = done;
     }
-    if (!ok) return F32PHASE ? PH_SWITCH : PH_LSFAIL;
+    if (!ok) return MODE == 0 ? PH_LSFAIL : PH_SWITCH;
 
     // ---- curvature pair, then move ------------------------------------------
     V sv[A][3], yv[A][3];
@@ -412,7 +473,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
       for (int c = 0; c < 3; ++c) mv[0] = fmax(mv[0], abs_nan_inf(g[a][c]));
     mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (X)1 : (X)0;
     team_max<T, 2, X>(tm, mv);
-    if (mv[0] < stop_gtol) return F32PHASE ? PH_SWITCH : PH_CONVERGED;
+    if (mv[0] < stop_gtol) return MODE == 1 ? PH_SWITCH : PH_CONVERGED;
     if (mv[1] > (X)0) return PH_TIMEOUT;
   }
   return PH_MAXITER;
@@ -421,42 +482,52 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
 // ---------------------------------------------------------------------------
 // Minimise the cluster whose owned coordinates are in x64 (in place).
 // hist: this team's history slot (2 m A 3 T values of the phase's V type).
-// pos:  this team's shared position buffer (n PosD entries).
+// pos:  this team's shared position buffer (n entries of 32 bytes).
+// MIXED: FP32 phase, then polish iterations whose evaluations run in
+// double-float arithmetic; convergence is confirmed, and the returned energy
+// computed, by a true FP64 evaluation (if FP64 disagrees, polishing goes on).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int status_of(int code) {
+  return code == PH_CONVERGED ? ST_CONVERGED
+       : code == PH_LSFAIL   ? ST_LS_FAIL
+       : code == PH_TIMEOUT  ? ST_TIMEOUT : ST_MAXITER;
+}
+
 template <int T, int A, bool MIXED>
 __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const MinParams& p,
                          void* hist, void* pos, MinResult& r) {
   r.E = 0.0; r.status = ST_CONVERGED; r.iters = 0;
-  r.evals32 = 0; r.evals64 = 0; r.iters32 = 0; r.iters64 = 0; r.vec32 = 0; r.vec64 = 0;
+  r.evals32 = 0; r.evals64 = 0; r.evals_df = 0; r.iters32 = 0; r.iters64 = 0;
+  r.vec32 = 0; r.vec64 = 0;
   if (n <= 1) return;
   const long long t0 = clock64();
   int cnt = 0, head = 0, iters = 0;
   const size_t hstride = (size_t)p.m * A * 3 * T;
+  const double kInf = __longlong_as_double(0x7ff0000000000000LL);
   if constexpr (!MIXED) {
     double g[A][3];
     double f, dummy;
-    evaluate<T, A, double, double>(tm, n, x64, g, (PosD*)pos, p, nullptr, f, dummy);
+    evaluate<T, A, double, double>(tm, n, x64, g, pos, p, nullptr, f, dummy);
     r.evals64 = 1;
     const double gm = grad_max<T, A, double>(tm, g);
-    if (!isfinite(f) || !(gm < __longlong_as_double(0x7ff0000000000000LL))) {
+    if (!isfinite(f) || !(gm < kInf)) {
       r.E = f; r.status = ST_NONFINITE; return;
     }
     if (gm < p.gtol) { r.E = f; return; }
     double sy[LJ_MAX_M], yy[LJ_MAX_M];
     double* Sh = (double*)hist;
-    const int code = run_phase<T, A, double, double, false>(
+    const int code = run_phase<T, A, double, double, 0>(
         tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt, head, iters, r.evals64, r.iters64,
-        r.vec64, (PosD*)pos, p, t0);
+        r.vec64, pos, p, t0);
     r.E = f;
     r.iters = iters;
-    r.status = code == PH_CONVERGED ? ST_CONVERGED
-             : code == PH_LSFAIL   ? ST_LS_FAIL
-             : code == PH_TIMEOUT  ? ST_TIMEOUT : ST_MAXITER;
+    r.status = status_of(code);
   } else {
     float* Sh = (float*)hist;
     float* Yh = Sh + hstride;
     float sy[LJ_MAX_M], yy[LJ_MAX_M];
     int code = PH_SWITCH;
+    // ---- tier 1: FP32 -----------------------------------------------------
     {
       float x32[A][3], g32[A][3];
 #pragma unroll
@@ -465,13 +536,12 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         for (int c = 0; c < 3; ++c) x32[a][c] = (float)x64[a][c];
       ff f32;
       float dummy;
-      evaluate<T, A, float, float>(tm, n, x32, g32, (PosF*)pos, p, nullptr, f32, dummy);
+      evaluate<T, A, float, float>(tm, n, x32, g32, pos, p, nullptr, f32, dummy);
       r.evals32 = 1;
       const float gm = grad_max<T, A, float>(tm, g32);
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
-        code = run_phase<T, A, float, float, true>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt,
-                                                   head, iters, r.evals32, r.iters32, r.vec32,
-                                                   (PosF*)pos, p, t0);
+        code = run_phase<T, A, float, float, 1>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt, head,
+                                                iters, r.evals32, r.iters32, r.vec32, pos, p, t0);
         if (r.iters32 > 0) {
 #pragma unroll
           for (int a = 0; a < A; ++a)
@@ -480,30 +550,68 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         }
       }
     }
-    // FP64 evaluation at the hand-over point (also the final energy when the
-    // FP32 phase ran out of iterations or time)
     double g[A][3];
     double f, dummy;
-    evaluate<T, A, double, double>(tm, n, x64, g, (PosD*)pos, p, nullptr, f, dummy);
+    int status = -1;
+    bool need_fp64 = false;
+    if (code == PH_MAXITER || code == PH_TIMEOUT) {
+      status = status_of(code);
+    } else {
+      // ---- tier 2: double-float polish --------------------------------------
+      evaluate<T, A, double, double, 1>(tm, n, x64, g, pos, p, nullptr, f, dummy);
+      r.evals_df += 1;
+      double gm = grad_max<T, A, double>(tm, g);
+      if (!isfinite(f) || !(gm < kInf)) {
+        need_fp64 = true;                 // let FP64 judge the point
+      }
+      while (status < 0 && !need_fp64) {
+        if (gm < p.gtol) {
+          need_fp64 = true;               // confirm (and finish) in FP64
+          break;
+        }
+        code = run_phase<T, A, double, float, 2, 1>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
+                                                     iters, r.evals_df, r.iters64, r.vec64, pos,
+                                                     p, t0);
+        if (code == PH_CONVERGED) {
+          gm = 0.0;
+        } else if (code == PH_SWITCH) {
+          need_fp64 = true;
+        } else {
+          status = status_of(code);
+        }
+      }
+    }
+    if (need_fp64) {
+      // ---- tier 3: FP64 -------------------------------------------------------
+      evaluate<T, A, double, double>(tm, n, x64, g, pos, p, nullptr, f, dummy);
+      r.evals64 += 1;
+      const double gm = grad_max<T, A, double>(tm, g);
+      if (!isfinite(f) || !(gm < kInf)) {
+        r.E = f; r.iters = iters; r.status = ST_NONFINITE; return;
+      }
+      if (gm < p.gtol) {
+        r.E = f; r.iters = iters; r.status = ST_CONVERGED; return;
+      }
+      code = run_phase<T, A, double, float, 0>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
+                                               iters, r.evals64, r.iters64, r.vec64, pos, p, t0);
+      r.E = f;
+      r.iters = iters;
+      r.status = status_of(code);
+      return;
+    }
+    // final energy (and the non-finite test) in FP64
+    evaluate<T, A, double, double>(tm, n, x64, g, pos, p, nullptr, f, dummy);
     r.evals64 += 1;
     const double gm = grad_max<T, A, double>(tm, g);
     r.E = f;
-    if (!isfinite(f) || !(gm < __longlong_as_double(0x7ff0000000000000LL))) {
+    r.iters = iters;
+    if (!isfinite(f) || !(gm < kInf)) {
       r.status = ST_NONFINITE;
     } else if (gm < p.gtol) {
       r.status = ST_CONVERGED;
-    } else if (code == PH_MAXITER || code == PH_TIMEOUT) {
-      r.status = code == PH_MAXITER ? ST_MAXITER : ST_TIMEOUT;
     } else {
-      code = run_phase<T, A, double, float, false>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
-                                                   iters, r.evals64, r.iters64, r.vec64,
-                                                   (PosD*)pos, p, t0);
-      r.E = f;
-      r.status = code == PH_CONVERGED ? ST_CONVERGED
-               : code == PH_LSFAIL   ? ST_LS_FAIL
-               : code == PH_TIMEOUT  ? ST_TIMEOUT : ST_MAXITER;
+      r.status = status;
     }
-    r.iters = iters;
   }
 }
 

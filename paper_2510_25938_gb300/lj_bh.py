@@ -23,9 +23,9 @@ LJ_F32, LJ_F64 = 0, 1
 LJ_PREC_FP64, LJ_PREC_FP32, LJ_PREC_MIXED = 0, 1, 2
 (LJ_CAND_CONVERGED, LJ_CAND_MAXITER, LJ_CAND_LINESEARCH_FAIL, LJ_CAND_NONFINITE,
  LJ_CAND_TIMEOUT, LJ_CAND_BAD_INPUT) = range(6)
-LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 32
-STATS_FIELDS = ("evals32", "evals64", "iters32", "iters64", "pairs32", "pairs64",
-                "vec_elems32", "vec_elems64", "converged", "minimisations")
+LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 16
+STATS_FIELDS = ("evals32", "evals64", "evals_df", "iters32", "iters64", "pairs32", "pairs64",
+                "pairs_df", "vec_elems32", "vec_elems64", "converged", "minimisations")
 
 
 class LjError(RuntimeError):
