@@ -1,12 +1,14 @@
 #!/usr/bin/env python3
 """Benchmark: batched LJ38 Basin Hopping on GB300 (one JSON line on stdout).
 
-Workload (one "step" = one Basin Hopping step of every walker): LJ38
-(eps = sigma = 1), 64 independent walkers x K = 8 candidates per step
-(512 local minimisations per step), starts uniform in a cube of side
-3.2 sigma (seeded), minimised once before timing; perturbations +-step per
-coordinate from Philox (initial step 0.4 sigma, adapted every 10 steps toward
-50% acceptance), kT = 0.8, L-BFGS m = 10 to ||grad E||_inf < 1e-6.
+Workload: LJ38 (eps = sigma = 1), 64 independent walkers x K = 8 candidates
+per BH step (512 local minimisations per BH step), 500 BH steps, starts
+uniform in a cube of side 3.2 sigma (seeded), minimised once before timing;
+perturbations +-step per coordinate from Philox (initial step 0.4 sigma,
+adapted every 10 steps toward 50% acceptance), kT = 0.8, L-BFGS m = 10 to
+||grad E||_inf < 1e-6.  One bench "step" is one bh_step_batched launch that
+advances every walker by one adaptation window (10 BH steps = 5120 local
+minimisations); the default 50 steps run the workload's 500 BH steps.
 
 metric  converged LJ minimisations per second (minimisations that reached
         ||grad E||_inf < 1e-6 with an FP64 gradient), mixed precision path;
@@ -36,10 +38,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_ATOMS, WALKERS, K = 38, 64, 8
+BH_PER_LAUNCH = 10          # BH steps per bench step (one adaptation window)
 SIDE, STEP0, KT = 3.2, 0.4, 0.8
 CONFIG_ID = 1
-WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per step (512 L-BFGS "
-            "minimisations per step), cube starts side 3.2 sigma, m=10, ||g||_inf<1e-6")
+WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per BH step (512 L-BFGS "
+            "minimisations per BH step), 10 BH steps per bench step, cube starts side "
+            "3.2 sigma, m=10, ||g||_inf<1e-6")
 PAIRS = N_ATOMS * (N_ATOMS - 1) // 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 (FMA) x max SM GHz
 FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of GB300
@@ -48,7 +52,7 @@ FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of G
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None)
@@ -167,6 +171,8 @@ def run_reference(args):
     state = {"x_cur": xm.copy(), "e_cur": em.copy(), "x_best": xm.copy(), "e_best": em.copy(),
              "stepsize": np.full(WALKERS, STEP0), "win_accept": np.zeros(WALKERS, np.int32),
              "n_accept": np.zeros(WALKERS, np.int32)}
+    # each reference step is a bounded sample: one BH step of all 64 walkers
+    # (1/10 of a bench step's work), so that --steps K --warmup W ends in minutes
     for s in range(args.warmup):
         O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=s, n_steps=1))
     conv = mins = 0
@@ -180,13 +186,15 @@ def run_reference(args):
     v = conv / dt
     line = {"metric": "converged LJ minimisations/s", "value": v,
             "unit": "converged minimisations/s", "impl": "reference", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps * BH_PER_LAUNCH,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64"},
             "cpu_baseline": {"value": v, "unit": "converged minimisations/s",
                              "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"{args.steps} BH steps x 64 walkers x K=8 = {mins} "
-                                       f"FP64 minimisations ({conv} converged)"},
+                                       f"FP64 minimisations ({conv} converged); "
+                                       f"ms_per_step scaled to 10 BH steps"},
             "e2e": {"value": v, "unit": "converged minimisations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -231,10 +239,10 @@ def run_cuda(args):
 
     def timed_run(prec, n_steps, warmup):
         state = init_state()
-        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=1, walker0=walker0,
+        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH, walker0=walker0,
                        min=L.LbfgsParams(prec=prec))
         for s in range(warmup):
-            p.step0 = s
+            p.step0 = s * BH_PER_LAUNCH
             L.bh_step_batched(ctx, state, p)
         stats = L.new_stats(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -246,7 +254,7 @@ def run_cuda(args):
             t0 = time.perf_counter()
             for s in range(n_steps):
                 flush.fill_(float(s))
-                p.step0 = warmup + s
+                p.step0 = (warmup + s) * BH_PER_LAUNCH
                 ev[s][0].record(stream)
                 L.bh_step_batched(ctx, state, p, None, stats)
                 ev[s][1].record(stream)
@@ -261,7 +269,7 @@ def run_cuda(args):
         BH step, D2H of the updated state, every step."""
         dstate = init_state()
         host = {k: v.cpu().pin_memory() for k, v in dstate.items()}
-        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=1, walker0=walker0,
+        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH, walker0=walker0,
                        min=L.LbfgsParams(prec=prec))
         stats = L.new_stats(dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
@@ -274,7 +282,7 @@ def run_cuda(args):
                 t0 = time.perf_counter()
             for k in host:
                 dstate[k].copy_(host[k], non_blocking=True)
-            p.step0 = s
+            p.step0 = s * BH_PER_LAUNCH
             L.bh_step_batched(ctx, dstate, p, None, stats)
             for k in host:
                 host[k].copy_(dstate[k], non_blocking=True)
@@ -312,7 +320,7 @@ def run_cuda(args):
         ctx.close()
         return 0
     # ---- FP64 path on the same workload --------------------------------------
-    n64 = args.fp64_steps if args.fp64_steps is not None else max(3, args.steps // 8)
+    n64 = args.fp64_steps if args.fp64_steps is not None else max(2, args.steps // 10)
     t64, _, st64, _, _ = timed_run(L.LJ_PREC_FP64, n64, min(args.warmup, 3))
     t64 = max_over_ranks(t64)
     value64 = sum_over_ranks(st64["converged"]) / t64
@@ -320,7 +328,7 @@ def run_cuda(args):
     # ---- end to end -------------------------------------------------------------
     e2e = None
     if not args.no_e2e:
-        wall_e2e, st_e2e, h2d = e2e_run(L.LJ_PREC_MIXED, max(5, args.steps // 4),
+        wall_e2e, st_e2e, h2d = e2e_run(L.LJ_PREC_MIXED, max(3, args.steps // 5),
                                         min(args.warmup, 3))
         wall_e2e = max_over_ranks(wall_e2e)
         e2e = {"value": sum_over_ranks(st_e2e["converged"]) / wall_e2e,
@@ -340,7 +348,9 @@ def run_cuda(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_atoms": N_ATOMS, "walkers_per_gpu": WALKERS, "K": K,
-                   "minimisations_per_step": WALKERS * K * world, "precision": "mixed",
+                   "bh_steps_per_step": BH_PER_LAUNCH,
+                   "minimisations_per_step": WALKERS * K * BH_PER_LAUNCH * world,
+                   "precision": "mixed",
                    "l2": "flushed (256 MiB write) between timed steps"},
         "minimisations_per_s": mins / t_dev,
         "converged_fraction": conv / max(mins, 1),
@@ -349,7 +359,8 @@ def run_cuda(args):
                       "mixed_over_fp64": value / value64 if value64 > 0 else None,
                       "achieved_tflops": flops_64path / t64 / 1e12,
                       "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
-        "work": {k: st_mix[k] for k in ("evals32", "evals64", "evals_df", "iters32", "iters64")},
+        "work": {k: st_mix[k] for k in ("evals32", "evals64", "evals_df", "iters32", "iters64",
+                                        "cycles32", "cycles_df", "cycles64")},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,

@@ -163,6 +163,9 @@ typedef struct {
     unsigned long long vec_elems64; /* same for FP64 vectors */
     unsigned long long converged;   /* candidates with LJ_CAND_CONVERGED */
     unsigned long long minimisations; /* candidates minimised */
+    unsigned long long cycles32;    /* SM clock cycles in FP32 iterations (summed over candidates) */
+    unsigned long long cycles_df;   /* ... in double-float polish iterations */
+    unsigned long long cycles64;    /* ... in FP64 iterations and FP64 evaluations */
 } lj_stats;
 
 const char* lj_status_string(lj_status s);

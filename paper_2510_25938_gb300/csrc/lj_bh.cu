@@ -70,8 +70,9 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
   double* xbest = reinterpret_cast<double*>(sp);
   sp += align16((size_t)3 * n * sizeof(double));
   void* pos;
+  void* hbuf;
   long long* word;
-  carve_team<T>(sp, n, pos, tm.red, word);
+  carve_team<T>(sp, n, true, pos, hbuf, tm.red, word);
   const MinParams p = to_dev(a.p);
   void* hist = static_cast<unsigned char*>(a.hist) + ((size_t)w * K + k) * a.hist_slot_bytes;
   const uint32_t wg = (uint32_t)(a.walker0 + w);
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
       }
     }
     MinResult r;
-    minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, r);
+    minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, hbuf, r);
 #pragma unroll
     for (int sl = 0; sl < A; ++sl) {
       const int i = tm.rank + sl * T;
@@ -140,6 +141,9 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
         atomicAdd(&a.stats->vec_elems64, (unsigned long long)r.vec64);
         atomicAdd(&a.stats->converged, r.status == ST_CONVERGED ? 1ULL : 0ULL);
         atomicAdd(&a.stats->minimisations, 1ULL);
+        atomicAdd(&a.stats->cycles32, (unsigned long long)r.cyc32);
+        atomicAdd(&a.stats->cycles_df, (unsigned long long)r.cycdf);
+        atomicAdd(&a.stats->cycles64, (unsigned long long)r.cyc64);
       }
     }
     cl.sync();   // every candidate's energy and minimum are visible cluster-wide
@@ -214,7 +218,7 @@ cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out) {
   out->slots = (int64_t)n_walkers * K;
   out->team = T;
   if (K <= LJ_MAX_K) {                // one cluster of K CTAs per walker
-    const size_t smem = bhc_head_bytes<T>(n_atoms) + team_smem_bytes<T>(n_atoms);
+    const size_t smem = bhc_head_bytes<T>(n_atoms) + team_smem_bytes<T>(n_atoms, true);
     auto k = bh_cluster_kernel<T, A, MIXED>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

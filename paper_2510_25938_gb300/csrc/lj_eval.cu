@@ -22,7 +22,9 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
   tm.bar = team + 1;
   void* pos;
   long long* word;
-  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n), a.max_n, pos, tm.red, word);
+  void* hbuf;
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, false), a.max_n, false, pos, hbuf,
+                tm.red, word);
   MinParams p{};
   p.eps = a.eps;
   p.sigma = a.sigma;
@@ -52,8 +54,7 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
     }
     typename Tr<X>::F E;
     typename Tr<X>::S dummy;
-    evaluate<T, A, X, X>(tm, n, x, g, static_cast<typename PosOf<X>::type*>(pos), p, nullptr, E,
-                         dummy);
+    evaluate<T, A, X, X>(tm, n, x, g, pos, nullptr, p, nullptr, E, dummy);
     if (gout) {
 #pragma unroll
       for (int s = 0; s < A; ++s) {
@@ -72,7 +73,7 @@ template <int T, int A, typename X, typename IO>
 cudaError_t launch_one(const ljh::EvalArgs& a, cudaStream_t s) {
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
-  const size_t smem = TPC * team_smem_bytes<T>(a.max_n);
+  const size_t smem = TPC * team_smem_bytes<T>(a.max_n, false);
   auto k = eval_kernel<T, A, X, IO>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

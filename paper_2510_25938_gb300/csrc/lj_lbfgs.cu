@@ -30,7 +30,9 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
   tm.bar = team + 1;
   void* pos;
   long long* word;
-  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n), a.max_n, pos, tm.red, word);
+  void* hbuf;
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true), a.max_n, true, pos, hbuf,
+                tm.red, word);
   const MinParams p = to_dev(a.p);
   const long long slot = (long long)blockIdx.x * TPC + team;
   void* hist = static_cast<unsigned char*>(a.hist) + slot * a.hist_slot_bytes;
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
       for (int k = 0; k < 3; ++k) x64[s][k] = i < n ? a.x[3 * (a0 + i) + k] : 0.0;
     }
     MinResult r;
-    minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, r);
+    minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, hbuf, r);
 #pragma unroll
     for (int s = 0; s < A; ++s) {
       const int i = tm.rank + s * T;
@@ -102,6 +104,9 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
         atomicAdd(&a.stats->vec_elems64, (unsigned long long)r.vec64);
         atomicAdd(&a.stats->converged, r.status == ST_CONVERGED ? 1ULL : 0ULL);
         atomicAdd(&a.stats->minimisations, 1ULL);
+        atomicAdd(&a.stats->cycles32, (unsigned long long)r.cyc32);
+        atomicAdd(&a.stats->cycles_df, (unsigned long long)r.cycdf);
+        atomicAdd(&a.stats->cycles64, (unsigned long long)r.cyc64);
       }
     }
   }
@@ -111,7 +116,7 @@ template <int T, int A, bool MIXED>
 cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out) {
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
-  const size_t smem = TPC * team_smem_bytes<T>(max_n);
+  const size_t smem = TPC * team_smem_bytes<T>(max_n, true);
   auto k = lbfgs_kernel<T, A, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -48,6 +48,7 @@ struct MinResult {
   int iters;
   int evals32, evals64, evals_df, iters32, iters64;
   long long vec32, vec64;   // sum over iterations of (history used) * 3N
+  long long cyc32, cycdf, cyc64;   // SM clock cycles spent in each tier
 };
 
 enum : int { PH_CONVERGED = 0, PH_MAXITER = 1, PH_LSFAIL = 2, PH_SWITCH = 3, PH_TIMEOUT = 4 };
@@ -74,9 +75,11 @@ __device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
 // ---------------------------------------------------------------------------
 // PM = 0: pair terms in X precision; PM = 1 (X = double only): pair terms in
 // double-float arithmetic on coordinates scaled by 1/sigma.
+// hbuf: the team's half-pair buffer (24 bytes per pair) or nullptr; used for
+// FP64 / double-float evaluations, which then compute each pair once.
 template <int T, int A, typename X, typename V, int PM = 0>
 __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[A][3], X (&g)[A][3],
-                                         void* posv, const MinParams& p,
+                                         void* posv, void* hbuf, const MinParams& p,
                                          const V (*d)[3], typename Tr<X>::F& E,
                                          typename Tr<X>::S& dphi) {
   using S = typename Tr<X>::S;
@@ -101,6 +104,97 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
   }
   tm.sync();
   V dp = (V)0;
+  if constexpr (sizeof(X) == 8) {
+    if (hbuf != nullptr) {
+      // ---- half-pair evaluation ---------------------------------------------
+      const int np = n_pairs(n);
+      int i, j;
+      pair_start(n, tm.rank, i, j);
+      if constexpr (PM == 1) {
+        const PosDF* pos = static_cast<const PosDF*>(posv);
+        ff* vb = static_cast<ff*>(hbuf);
+        ff e{0.f, 0.f};
+        for (int q = tm.rank; q < np; q += T) {
+          ff vx, vy, vz, ep;
+          pair_term_df(pos[i], pos[j], vx, vy, vz, ep);
+          vb[q] = vx; vb[np + q] = vy; vb[2 * np + q] = vz;
+          e = df_add(e, ep);
+          pair_advance(n, T, i, j);
+        }
+        tm.sync();
+        const double gs = 24.0 * p.eps / p.sigma;
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int ii = tm.rank + a * T;
+          if (ii < n) {
+            ff sx{0.f, 0.f}, sy{0.f, 0.f}, sz{0.f, 0.f};
+            for (int jj = 0; jj < n; ++jj) {
+              if (jj == ii) continue;
+              const int q = jj > ii ? pair_index(n, ii, jj) : pair_index(n, jj, ii);
+              ff vx = vb[q], vy = vb[np + q], vz = vb[2 * np + q];
+              if (jj < ii) {
+                vx = ff{-vx.hi, -vx.lo}; vy = ff{-vy.hi, -vy.lo}; vz = ff{-vz.hi, -vz.lo};
+              }
+              sx = df_add(sx, vx); sy = df_add(sy, vy); sz = df_add(sz, vz);
+            }
+            g[a][0] = -gs * df_to_double(sx);
+            g[a][1] = -gs * df_to_double(sy);
+            g[a][2] = -gs * df_to_double(sz);
+          } else {
+            g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+          }
+          if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+        }
+        E = team_sum_dd<T>(tm, dd_two_sum((double)e.hi, (double)e.lo)) * (4.0 * p.eps);
+      } else {
+        const PosD* pos = static_cast<const PosD*>(posv);
+        double* vb = static_cast<double*>(hbuf);
+        const double sig2 = p.sigma * p.sigma;
+        dd e{0.0, 0.0};
+        double eb = 0.0;
+        int blk = 0;
+        for (int q = tm.rank; q < np; q += T) {
+          double vx, vy, vz, ep;
+          pair_term_f64(pos[i], pos[j], sig2, vx, vy, vz, ep);
+          vb[q] = vx; vb[np + q] = vy; vb[2 * np + q] = vz;
+          eb += ep;
+          if (++blk == 4) {           // fold 4-term blocks into the compensated sum
+            dd t = dd_two_sum(e.hi, eb);
+            e.hi = t.hi; e.lo = __dadd_rn(e.lo, t.lo);
+            eb = 0.0; blk = 0;
+          }
+          pair_advance(n, T, i, j);
+        }
+        {
+          dd t = dd_two_sum(e.hi, eb);
+          e.hi = t.hi; e.lo = __dadd_rn(e.lo, t.lo);
+        }
+        tm.sync();
+        const double gs = 24.0 * p.eps / sig2;
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int ii = tm.rank + a * T;
+          if (ii < n) {
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int jj = 0; jj < n; ++jj) {
+              if (jj == ii) continue;
+              const int q = jj > ii ? pair_index(n, ii, jj) : pair_index(n, jj, ii);
+              const double sgn = jj > ii ? 1.0 : -1.0;
+              sx = fma(sgn, vb[q], sx); sy = fma(sgn, vb[np + q], sy); sz = fma(sgn, vb[2 * np + q], sz);
+            }
+            g[a][0] = -gs * sx; g[a][1] = -gs * sy; g[a][2] = -gs * sz;
+          } else {
+            g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+          }
+          if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+        }
+        E = team_sum_dd<T>(tm, e) * (4.0 * p.eps);
+      }
+      if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+      tm.sync();   // the buffer is reused by the next evaluation
+      return;
+    }
+  }
   if constexpr (PM == 1) {
     static_assert(sizeof(X) == 8, "double-float pairs work on FP64 coordinates");
     const PosDF* pos = static_cast<const PosDF*>(posv);
@@ -229,7 +323,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
                          typename Tr<X>::F& f, V* __restrict__ Sh, V* __restrict__ Yh,
                          V (&sy)[LJ_MAX_M], V (&yy)[LJ_MAX_M], int& cnt, int& head, int& iters,
                          int& evals, int& phase_iters, long long& vec, void* pos,
-                         const MinParams& p, long long t0) {
+                         void* hbuf, const MinParams& p, long long t0) {
   using S = typename Tr<X>::S;
   using F = typename Tr<X>::F;
   const int m = p.m;
@@ -356,7 +450,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         for (int aa = 0; aa < A; ++aa)
 #pragma unroll
           for (int c = 0; c < 3; ++c) xt[aa][c] = x[aa][c] + (X)al * (X)d[aa][c];
-        evaluate<T, A, X, V, PM>(tm, n, xt, gt, pos, p, d, fo, dpo);
+        evaluate<T, A, X, V, PM>(tm, n, xt, gt, pos, hbuf, p, d, fo, dpo);
         ++ev;
         last_a = al;
       };
@@ -483,6 +577,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
 // Minimise the cluster whose owned coordinates are in x64 (in place).
 // hist: this team's history slot (2 m A 3 T values of the phase's V type).
 // pos:  this team's shared position buffer (n entries of 32 bytes).
+// hbuf: this team's half-pair buffer (24 n(n-1)/2 bytes) or nullptr.
 // MIXED: FP32 phase, then polish iterations whose evaluations run in
 // double-float arithmetic; convergence is confirmed, and the returned energy
 // computed, by a true FP64 evaluation (if FP64 disagrees, polishing goes on).
@@ -495,19 +590,26 @@ __device__ __forceinline__ int status_of(int code) {
 
 template <int T, int A, bool MIXED>
 __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const MinParams& p,
-                         void* hist, void* pos, MinResult& r) {
+                         void* hist, void* pos, void* hbuf, MinResult& r) {
   r.E = 0.0; r.status = ST_CONVERGED; r.iters = 0;
   r.evals32 = 0; r.evals64 = 0; r.evals_df = 0; r.iters32 = 0; r.iters64 = 0;
   r.vec32 = 0; r.vec64 = 0;
+  r.cyc32 = 0; r.cycdf = 0; r.cyc64 = 0;
   if (n <= 1) return;
   const long long t0 = clock64();
+  long long tmark = t0;
+  auto lap = [&](long long& acc) {
+    const long long t = clock64();
+    acc += t - tmark;
+    tmark = t;
+  };
   int cnt = 0, head = 0, iters = 0;
   const size_t hstride = (size_t)p.m * A * 3 * T;
   const double kInf = __longlong_as_double(0x7ff0000000000000LL);
   if constexpr (!MIXED) {
     double g[A][3];
     double f, dummy;
-    evaluate<T, A, double, double>(tm, n, x64, g, pos, p, nullptr, f, dummy);
+    evaluate<T, A, double, double>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
     r.evals64 = 1;
     const double gm = grad_max<T, A, double>(tm, g);
     if (!isfinite(f) || !(gm < kInf)) {
@@ -518,10 +620,11 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
     double* Sh = (double*)hist;
     const int code = run_phase<T, A, double, double, 0>(
         tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt, head, iters, r.evals64, r.iters64,
-        r.vec64, pos, p, t0);
+        r.vec64, pos, hbuf, p, t0);
     r.E = f;
     r.iters = iters;
     r.status = status_of(code);
+    lap(r.cyc64);
   } else {
     float* Sh = (float*)hist;
     float* Yh = Sh + hstride;
@@ -536,12 +639,13 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         for (int c = 0; c < 3; ++c) x32[a][c] = (float)x64[a][c];
       ff f32;
       float dummy;
-      evaluate<T, A, float, float>(tm, n, x32, g32, pos, p, nullptr, f32, dummy);
+      evaluate<T, A, float, float>(tm, n, x32, g32, pos, nullptr, p, nullptr, f32, dummy);
       r.evals32 = 1;
       const float gm = grad_max<T, A, float>(tm, g32);
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
         code = run_phase<T, A, float, float, 1>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt, head,
-                                                iters, r.evals32, r.iters32, r.vec32, pos, p, t0);
+                                                iters, r.evals32, r.iters32, r.vec32, pos, nullptr,
+                                                p, t0);
         if (r.iters32 > 0) {
 #pragma unroll
           for (int a = 0; a < A; ++a)
@@ -550,6 +654,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         }
       }
     }
+    lap(r.cyc32);
     double g[A][3];
     double f, dummy;
     int status = -1;
@@ -558,7 +663,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       status = status_of(code);
     } else {
       // ---- tier 2: double-float polish --------------------------------------
-      evaluate<T, A, double, double, 1>(tm, n, x64, g, pos, p, nullptr, f, dummy);
+      evaluate<T, A, double, double, 1>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
       r.evals_df += 1;
       double gm = grad_max<T, A, double>(tm, g);
       if (!isfinite(f) || !(gm < kInf)) {
@@ -571,7 +676,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         }
         code = run_phase<T, A, double, float, 2, 1>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
                                                      iters, r.evals_df, r.iters64, r.vec64, pos,
-                                                     p, t0);
+                                                     hbuf, p, t0);
         if (code == PH_CONVERGED) {
           gm = 0.0;
         } else if (code == PH_SWITCH) {
@@ -581,26 +686,29 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         }
       }
     }
+    lap(r.cycdf);
     if (need_fp64) {
       // ---- tier 3: FP64 -------------------------------------------------------
-      evaluate<T, A, double, double>(tm, n, x64, g, pos, p, nullptr, f, dummy);
+      evaluate<T, A, double, double>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
       r.evals64 += 1;
       const double gm = grad_max<T, A, double>(tm, g);
       if (!isfinite(f) || !(gm < kInf)) {
-        r.E = f; r.iters = iters; r.status = ST_NONFINITE; return;
+        r.E = f; r.iters = iters; r.status = ST_NONFINITE; lap(r.cyc64); return;
       }
       if (gm < p.gtol) {
-        r.E = f; r.iters = iters; r.status = ST_CONVERGED; return;
+        r.E = f; r.iters = iters; r.status = ST_CONVERGED; lap(r.cyc64); return;
       }
       code = run_phase<T, A, double, float, 0>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
-                                               iters, r.evals64, r.iters64, r.vec64, pos, p, t0);
+                                               iters, r.evals64, r.iters64, r.vec64, pos, hbuf, p,
+                                               t0);
       r.E = f;
       r.iters = iters;
       r.status = status_of(code);
+      lap(r.cyc64);
       return;
     }
     // final energy (and the non-finite test) in FP64
-    evaluate<T, A, double, double>(tm, n, x64, g, pos, p, nullptr, f, dummy);
+    evaluate<T, A, double, double>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
     r.evals64 += 1;
     const double gm = grad_max<T, A, double>(tm, g);
     r.E = f;
@@ -612,6 +720,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
     } else {
       r.status = status;
     }
+    lap(r.cyc64);
   }
 }
 

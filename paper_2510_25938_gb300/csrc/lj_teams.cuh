@@ -25,18 +25,30 @@ __host__ __device__ constexpr int cta_threads_for(int T) { return T < 128 ? 128 
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// per-team shared bytes: positions (as FP64 quads; the FP32 phase uses the
-// first half of the same buffer), cross-warp reduction scratch, one word
+// Half-pair buffers are used for clusters of up to kHalfMaxN atoms.
+constexpr int kHalfMaxN = 64;
+
+__host__ __device__ constexpr size_t half_bytes(int max_n, bool half) {
+  return (half && max_n <= kHalfMaxN) ? align16((size_t)24 * (max_n * (max_n - 1) / 2)) : 0;
+}
+
+// per-team shared bytes: positions (32-byte records; the FP32 phase uses the
+// first half of the same buffer), the optional half-pair buffer, cross-warp
+// reduction scratch, one word
 template <int T>
-__host__ __device__ constexpr size_t team_smem_bytes(int max_n) {
-  return align16((size_t)max_n * sizeof(PosD)) + (T > 32 ? 8 * (T / 32) * sizeof(double) : 0) + 16;
+__host__ __device__ constexpr size_t team_smem_bytes(int max_n, bool half) {
+  return align16((size_t)max_n * sizeof(PosD)) + half_bytes(max_n, half) +
+         (T > 32 ? 8 * (T / 32) * sizeof(double) : 0) + 16;
 }
 
 template <int T>
-__device__ __forceinline__ void carve_team(unsigned char* base, int max_n, void*& pos, double*& red,
-                                           long long*& word) {
+__device__ __forceinline__ void carve_team(unsigned char* base, int max_n, bool half, void*& pos,
+                                           void*& hbuf, double*& red, long long*& word) {
   pos = base;
   unsigned char* p = base + align16((size_t)max_n * sizeof(PosD));
+  const size_t hb = half_bytes(max_n, half);
+  hbuf = hb ? static_cast<void*>(p) : nullptr;
+  p += hb;
   red = reinterpret_cast<double*>(p);
   p += (T > 32 ? 8 * (T / 32) * sizeof(double) : 0);
   word = reinterpret_cast<long long*>(p);

@@ -25,7 +25,8 @@ LJ_PREC_FP64, LJ_PREC_FP32, LJ_PREC_MIXED = 0, 1, 2
  LJ_CAND_TIMEOUT, LJ_CAND_BAD_INPUT) = range(6)
 LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 16
 STATS_FIELDS = ("evals32", "evals64", "evals_df", "iters32", "iters64", "pairs32", "pairs64",
-                "pairs_df", "vec_elems32", "vec_elems64", "converged", "minimisations")
+                "pairs_df", "vec_elems32", "vec_elems64", "converged", "minimisations",
+                "cycles32", "cycles_df", "cycles64")
 
 
 class LjError(RuntimeError):
