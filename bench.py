@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-micro", action="store_true", help="skip the evaluation microbench")
     ap.add_argument("--profile", action="store_true",
                     help="mixed-precision steps only (no FP64 arm, e2e or CPU legs): the "
                          "command to run under ncu; numbers printed then are not bench values")
@@ -158,6 +159,53 @@ def cpu_baseline(x0, seed, budget_s=12.0):
             "kind": "oracle",
             "sample": f"{steps} BH steps x 64 walkers x K=8 = {mins} FP64 minimisations of LJ38 "
                       f"({conv} converged) in {dt:.1f} s"}
+
+
+def eval_microbench(L, ctx, dev, flush, repeats=100):
+    """Energy+gradient throughput on 65,536 LJ38 configurations: 1,024 local
+    minima (GPU FP64 minimiser from seeded cube starts of side 3.2 sigma) x 64
+    Gaussian jitters (sigma_x = 0.05 sigma), FP32 and FP64, `repeats` timed
+    sweeps each with L2 flushed between sweeps; pair evaluations per second
+    (703 unordered pairs per configuration) and algorithmic TFLOP/s
+    (28 flops per pair) against the FP32 / FP64 non-tensor peaks."""
+    import torch
+    from paper_2510_25938_gb300 import inputs as I
+    seed = I.workload_seed(2)
+    x0 = I.cube_starts(1024, N_ATOMS, SIDE, seed)
+    x = torch.as_tensor(x0.reshape(-1), dtype=torch.float64, device=dev).contiguous()
+    e = torch.empty(1024, dtype=torch.float64, device=dev)
+    L.lbfgs_minimize_batched(ctx, x, e, n_cand=1024, uniform_n=N_ATOMS,
+                             params=L.LbfgsParams(prec=L.LJ_PREC_FP64))
+    minima = x.view(1024, -1).cpu().numpy()
+    cfg = I.jitter(np.repeat(minima, 64, axis=0), 0.05, seed + 1)
+    n_cand = cfg.shape[0]
+    pairs = n_cand * PAIRS
+    out = {"configs": n_cand, "repeats": repeats, "pairs_per_sweep": pairs}
+    stream = torch.cuda.current_stream()
+    for name, dt, prec, peak in (("fp32", torch.float32, L.LJ_PREC_FP32, FP32_PEAK_TFLOPS),
+                                 ("fp64", torch.float64, L.LJ_PREC_FP64, FP64_PEAK_TFLOPS)):
+        xd = torch.as_tensor(cfg.reshape(-1), dtype=dt, device=dev).contiguous()
+        en = torch.empty(n_cand, dtype=torch.float64, device=dev)
+        gr = torch.empty_like(xd)
+        for _ in range(3):
+            L.lj_energy_grad_batched(ctx, xd, en, gr, n_cand=n_cand, uniform_n=N_ATOMS, prec=prec)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(repeats)]
+        torch.cuda.synchronize()
+        for r in range(repeats):
+            flush.fill_(float(r))
+            ev[r][0].record(stream)
+            L.lj_energy_grad_batched(ctx, xd, en, gr, n_cand=n_cand, uniform_n=N_ATOMS, prec=prec)
+            ev[r][1].record(stream)
+        torch.cuda.synchronize()
+        t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        rate = pairs * repeats / t
+        out[name] = {"pair_evals_per_s": rate, "ms_per_sweep": 1e3 * t / repeats,
+                     "achieved_tflops": 28.0 * rate / 1e12, "peak_tflops": peak,
+                     "frac": 28.0 * rate / 1e12 / peak,
+                     "hbm_gbs": (xd.numel() * xd.element_size() * 2 + 8 * n_cand) * repeats / t / 1e9}
+    out["peaks"] = "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz; FP64: nominal 1.25 TFLOP/s"
+    return out
 
 
 def run_reference(args):
@@ -325,6 +373,10 @@ def run_cuda(args):
     t64 = max_over_ranks(t64)
     value64 = sum_over_ranks(st64["converged"]) / t64
     flops_64path, _ = flops_from_stats(st64)
+    # ---- evaluation microbench (pair evals/s) ---------------------------------
+    micro = None
+    if not args.no_micro and world == 1:
+        micro = eval_microbench(L, ctx, dev, flush)
     # ---- end to end -------------------------------------------------------------
     e2e = None
     if not args.no_e2e:
@@ -372,6 +424,8 @@ def run_cuda(args):
                             "fp64_flop_share": flops64 / flops if flops else None}
     if e2e:
         line["e2e"] = e2e
+    if micro:
+        line["eval_microbench"] = micro
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(x0, seed)
     if rank == 0:

@@ -166,7 +166,22 @@ typedef struct {
     unsigned long long cycles32;    /* SM clock cycles in FP32 iterations (summed over candidates) */
     unsigned long long cycles_df;   /* ... in double-float polish iterations */
     unsigned long long cycles64;    /* ... in FP64 iterations and FP64 evaluations */
+    unsigned long long cycles_direction;  /* ... of which in L-BFGS direction computations */
+    unsigned long long cycles_linesearch; /* ... of which in line searches (with their evaluations) */
 } lj_stats;
+
+/* Tuning options of a context. */
+typedef enum {
+    LJ_OPT_BH_TEAM = 1,      /* threads per candidate in bh_step_batched for
+                                clusters of <= 64 atoms: 0 (automatic), 32, 64, 128 */
+    LJ_OPT_LBFGS_TEAM = 2,   /* the same for lbfgs_minimize_batched */
+    LJ_OPT_F32_HANDOVER = 3, /* MIXED: the FP32 phase hands over once the predicted
+                                decrease -alpha phi'(0) falls below this many FP32
+                                ulps of |E| (1..4096; 0 = default 4) */
+    LJ_OPT_DF_HANDOVER = 4   /* MIXED: the double-float polish hands over to FP64
+                                once the predicted decrease falls below this many
+                                2^-48 |E| (1..65536; 0 = default 32) */
+} lj_option;
 
 const char* lj_status_string(lj_status s);
 
@@ -178,6 +193,8 @@ lj_status lj_ctx_destroy(lj_ctx* ctx);
  * for bh_step_batched) of up to max_n atoms and history length max_m.  After
  * a reservation no call allocates. */
 lj_status lj_ctx_reserve(lj_ctx* ctx, int64_t max_cand, int32_t max_n, int32_t max_m);
+/* Set a tuning option (lj_option); affects later calls on this ctx only. */
+lj_status lj_ctx_set_option(lj_ctx* ctx, lj_option opt, int64_t value);
 /* Human-readable description of the last error on this ctx ("" if none). */
 const char* lj_ctx_last_error(const lj_ctx* ctx);
 

@@ -18,6 +18,10 @@ struct lj_ctx {
   size_t ws_bytes = 0;
   bool reserved = false;
   unsigned long long* queue = nullptr; // persistent-kernel work counter
+  int bh_team = 0;                     // LJ_OPT_BH_TEAM (0 = automatic)
+  int lbfgs_team = 0;                  // LJ_OPT_LBFGS_TEAM (0 = automatic)
+  int f32_handover = 4;                // LJ_OPT_F32_HANDOVER (FP32 ulps of |E|)
+  int df_handover = 32;                // LJ_OPT_DF_HANDOVER (2^-48 |E| units)
   std::string last_error;
 };
 
@@ -51,6 +55,9 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 // of that bound, FP64 history) -- used only to size reservations
 size_t slot_bytes_bound(int max_n, int m) {
   int T = 32, A = 1;
+  if (max_n <= 64) {               // any team choice: T * A <= 128
+    return (2 * (size_t)m * 128 * 3 * sizeof(double) + 15) & ~size_t(15);
+  }
   if (max_n > 32) A = 2;
   if (max_n > 64) T = 64;
   if (max_n > 128) T = 128;
@@ -116,8 +123,10 @@ lj_status check_min(lj_ctx* ctx, const lj_lbfgs_params* p) {
   return LJ_OK;
 }
 
-ljh::MinParamsH to_host(const lj_lbfgs_params* p) {
+ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p) {
   ljh::MinParamsH h;
+  h.f32_resolution = ctx->f32_handover * 5.9604644775390625e-8;    // ulps of 2^-24
+  h.df_resolution = ctx->df_handover * 3.552713678800501e-15;      // units of 2^-48
   h.m = p->m; h.max_iter = p->max_iter; h.max_ls = p->max_ls;
   h.gtol = p->gtol; h.c1 = p->c1; h.c2 = p->c2; h.alpha_max = p->alpha_max;
   h.switch_gtol = p->switch_gtol; h.deadline = p->deadline_cycles;
@@ -185,6 +194,27 @@ lj_status lj_ctx_reserve(lj_ctx* ctx, int64_t max_cand, int32_t max_n, int32_t m
   return LJ_OK;
 }
 
+lj_status lj_ctx_set_option(lj_ctx* ctx, lj_option opt, int64_t value) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  switch (opt) {
+    case LJ_OPT_BH_TEAM:
+    case LJ_OPT_LBFGS_TEAM:
+      if (value != 0 && value != 32 && value != 64 && value != 128)
+        return fail(ctx, LJ_ERR_INVALID_ARG, "team size must be 0 (automatic), 32, 64 or 128");
+      (opt == LJ_OPT_BH_TEAM ? ctx->bh_team : ctx->lbfgs_team) = (int)value;
+      return LJ_OK;
+    case LJ_OPT_F32_HANDOVER:
+      if (value < 0 || value > 4096) return fail(ctx, LJ_ERR_INVALID_ARG, "F32 handover 0..4096");
+      ctx->f32_handover = value ? (int)value : 4;
+      return LJ_OK;
+    case LJ_OPT_DF_HANDOVER:
+      if (value < 0 || value > 65536) return fail(ctx, LJ_ERR_INVALID_ARG, "DF handover 0..65536");
+      ctx->df_handover = value ? (int)value : 32;
+      return LJ_OK;
+  }
+  return fail(ctx, LJ_ERR_INVALID_ARG, "unknown option");
+}
+
 const char* lj_ctx_last_error(const lj_ctx* ctx) {
   return ctx ? ctx->last_error.c_str() : "NULL ctx";
 }
@@ -245,7 +275,10 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
   const int mixed = p->prec == LJ_PREC_MIXED;
   ljh::Plan plan;
-  cudaError_t e = ljh::lbfgs_plan(max_n, p->m, mixed, batch->n_cand, ctx->device, &plan);
+  cudaError_t e = mixed ? ljh::lbfgs_plan_mixed(max_n, p->m, batch->n_cand, ctx->device,
+                                                ctx->lbfgs_team, &plan)
+                        : ljh::lbfgs_plan_fp64(max_n, p->m, batch->n_cand, ctx->device,
+                                               ctx->lbfgs_team, &plan);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched plan");
   st = ensure_ws(ctx, (size_t)plan.slots * plan.slot_bytes);
   if (st != LJ_OK) return st;
@@ -254,7 +287,7 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   a.uniform_n = batch->uniform_n;
   a.off = batch->d_atom_offset;
   a.max_n = max_n;
-  a.p = to_host(p);
+  a.p = to_host(ctx, p);
   a.mixed = mixed;
   a.x = d_x;
   a.energy = d_energy;
@@ -265,7 +298,9 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   a.queue = ctx->queue;
   a.hist = ctx->ws;
   a.hist_slot_bytes = plan.slot_bytes;
-  e = ljh::lbfgs_launch(a, plan, (cudaStream_t)stream);
+  a.hist_on_chip = plan.hist_on_chip;
+  e = mixed ? ljh::lbfgs_launch_mixed(a, plan, (cudaStream_t)stream)
+            : ljh::lbfgs_launch_fp64(a, plan, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
   return LJ_OK;
 }
@@ -295,7 +330,10 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
   const int mixed = p->min.prec == LJ_PREC_MIXED;
   ljh::Plan plan;
-  cudaError_t e = ljh::bh_plan(s->n_atoms, p->min.m, mixed, s->n_walkers, p->K, &plan);
+  cudaError_t e = mixed ? ljh::bh_plan_mixed(s->n_atoms, p->min.m, s->n_walkers, p->K,
+                                             ctx->bh_team, &plan)
+                        : ljh::bh_plan_fp64(s->n_atoms, p->min.m, s->n_walkers, p->K,
+                                            ctx->bh_team, &plan);
   if (e == cudaErrorNotSupported)
     return fail(ctx, LJ_ERR_UNSUPPORTED,
                 "bh_step_batched supports clusters of up to 256 atoms in this build");
@@ -310,7 +348,7 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   a.K = p->K; a.kT = p->kT; a.target_rate = p->target_rate; a.factor = p->factor;
   a.interval = p->interval; a.seed = p->seed; a.step0 = p->step0; a.n_steps = p->n_steps;
   a.walker0 = p->walker0;
-  a.p = to_host(&p->min);
+  a.p = to_host(ctx, &p->min);
   a.mixed = mixed;
   if (trace) {
     a.tr = *trace;
@@ -320,7 +358,9 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   a.stats = d_stats;
   a.hist = ctx->ws;
   a.hist_slot_bytes = plan.slot_bytes;
-  e = ljh::bh_launch(a, plan, (cudaStream_t)stream);
+  a.hist_on_chip = plan.hist_on_chip;
+  e = mixed ? ljh::bh_launch_mixed(a, plan, (cudaStream_t)stream)
+            : ljh::bh_launch_fp64(a, plan, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "bh_step_batched launch");
   return LJ_OK;
 }

@@ -1,4 +1,4 @@
-// lj_bh.cu -- bh_step_batched: whole Basin Hopping steps in one launch.
+// lj_bh.cuh -- bh_step_batched: whole Basin Hopping steps in one launch.
 //
 // One CTA per walker; its K teams (one per candidate) run, for each step
 // (arXiv 2510.25938, Methodology, "Algorithm Overview"):
@@ -16,6 +16,7 @@
 // memory for all n_steps; after the minimisations the CTAs read each other's
 // energies and the winner's coordinates through distributed shared memory,
 // and every CTA takes the same (deterministic) decision.
+#pragma once
 #include <cooperative_groups.h>
 
 #include "lj_internal.h"
@@ -24,7 +25,7 @@
 
 namespace cg = cooperative_groups;
 
-namespace {
+namespace ljbh {
 
 using namespace ljd;
 
@@ -33,6 +34,7 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
   p.m = h.m; p.max_iter = h.max_iter; p.max_ls = h.max_ls;
   p.gtol = h.gtol; p.c1 = h.c1; p.c2 = h.c2; p.alpha_max = h.alpha_max;
   p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.eps = h.eps; p.sigma = h.sigma;
+  p.f32_resolution = h.f32_resolution; p.df_resolution = h.df_resolution;
   return p;
 }
 
@@ -71,10 +73,13 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
   sp += align16((size_t)3 * n * sizeof(double));
   void* pos;
   void* hbuf;
+  void* hist;
   long long* word;
-  carve_team<T>(sp, n, true, pos, hbuf, tm.red, word);
+  carve_team<T>(sp, n, true, a.hist_on_chip ? a.hist_slot_bytes : 0, pos, hbuf, hist, tm.red,
+                word);
   const MinParams p = to_dev(a.p);
-  void* hist = static_cast<unsigned char*>(a.hist) + ((size_t)w * K + k) * a.hist_slot_bytes;
+  if (!a.hist_on_chip)
+    hist = static_cast<unsigned char*>(a.hist) + ((size_t)w * K + k) * a.hist_slot_bytes;
   const uint32_t wg = (uint32_t)(a.walker0 + w);
   const int n3 = 3 * n;
 
@@ -144,6 +149,8 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
         atomicAdd(&a.stats->cycles32, (unsigned long long)r.cyc32);
         atomicAdd(&a.stats->cycles_df, (unsigned long long)r.cycdf);
         atomicAdd(&a.stats->cycles64, (unsigned long long)r.cyc64);
+        atomicAdd(&a.stats->cycles_direction, (unsigned long long)r.cycdir);
+        atomicAdd(&a.stats->cycles_linesearch, (unsigned long long)r.cycls);
       }
     }
     cl.sync();   // every candidate's energy and minimum are visible cluster-wide
@@ -215,10 +222,14 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
 template <int T, int A, bool MIXED>
 cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out) {
   out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
-  out->slots = (int64_t)n_walkers * K;
   out->team = T;
   if (K <= LJ_MAX_K) {                // one cluster of K CTAs per walker
-    const size_t smem = bhc_head_bytes<T>(n_atoms) + team_smem_bytes<T>(n_atoms, true);
+    const bool on_chip = bhc_head_bytes<T>(n_atoms) +
+                         team_smem_bytes<T>(n_atoms, true, out->slot_bytes) <= kSmemBudget;
+    out->hist_on_chip = on_chip ? 1 : 0;
+    out->slots = on_chip ? 0 : (int64_t)n_walkers * K;
+    const size_t smem = bhc_head_bytes<T>(n_atoms) +
+                        team_smem_bytes<T>(n_atoms, true, on_chip ? out->slot_bytes : 0);
     auto k = bh_cluster_kernel<T, A, MIXED>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -252,15 +263,21 @@ cudaError_t launch_cluster(const ljh::BhArgs& a, const ljh::Plan& plan, cudaStre
   return cudaLaunchKernelEx(&cfg, bh_cluster_kernel<T, A, MIXED>, a);
 }
 
-}  // namespace
+}  // namespace ljbh
 
-namespace ljh {
+namespace ljbh {
 
-// Basin Hopping runs one candidate per CTA with the team sizes up to 128
-// threads (clusters of up to 256 atoms).
+// Team size for one candidate: the default by cluster size (64 threads for
+// 33..64 atoms), or the team chosen with LJ_OPT_BH_TEAM (32 / 64 / 128
+// threads) for clusters of up to 64 atoms.
 template <class F>
-static cudaError_t dispatch_bh(int n, F&& f) {
+cudaError_t dispatch_bh(int n, int team, F&& f) {
   using std::integral_constant;
+  // measured on GB300 (LJ38, 64 walkers x K=8): 64 threads per candidate beat
+  // 32 (one warp, two atoms per thread) and 128 (fewer clusters resident)
+  if (team == 0 && n > 32 && n <= 64) team = 64;
+  if (n <= 64 && team == 64) return f(integral_constant<int, 64>{}, integral_constant<int, 1>{});
+  if (n <= 64 && team == 128) return f(integral_constant<int, 128>{}, integral_constant<int, 1>{});
   if (n <= 32) return f(integral_constant<int, 32>{}, integral_constant<int, 1>{});
   if (n <= 64) return f(integral_constant<int, 32>{}, integral_constant<int, 2>{});
   if (n <= 128) return f(integral_constant<int, 64>{}, integral_constant<int, 2>{});
@@ -268,24 +285,20 @@ static cudaError_t dispatch_bh(int n, F&& f) {
   return cudaErrorNotSupported;
 }
 
-cudaError_t bh_plan(int n_atoms, int m, int mixed, int n_walkers, int K, Plan* out) {
-  return dispatch_bh(n_atoms, [&](auto TT, auto AA) -> cudaError_t {
-    constexpr int T = decltype(TT)::value;
-    constexpr int A = decltype(AA)::value;
-    return mixed ? plan_one<T, A, true>(n_atoms, m, n_walkers, K, out)
-                 : plan_one<T, A, false>(n_atoms, m, n_walkers, K, out);
+template <bool MIXED>
+cudaError_t plan_impl(int n_atoms, int m, int n_walkers, int K, int team, ljh::Plan* out) {
+  return dispatch_bh(n_atoms, team, [&](auto TT, auto AA) -> cudaError_t {
+    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(n_atoms, m, n_walkers, K, out);
   });
 }
 
-cudaError_t bh_launch(const BhArgs& a, const Plan& plan, cudaStream_t s) {
-  return dispatch_bh(a.n_atoms, [&](auto TT, auto AA) -> cudaError_t {
-    constexpr int T = decltype(TT)::value;
-    constexpr int A = decltype(AA)::value;
-    cudaError_t e = a.mixed ? launch_cluster<T, A, true>(a, plan, s)
-                            : launch_cluster<T, A, false>(a, plan, s);
+template <bool MIXED>
+cudaError_t launch_impl(const ljh::BhArgs& a, const ljh::Plan& plan, cudaStream_t s) {
+  return dispatch_bh(a.n_atoms, plan.team, [&](auto TT, auto AA) -> cudaError_t {
+    cudaError_t e = launch_cluster<decltype(TT)::value, decltype(AA)::value, MIXED>(a, plan, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   });
 }
 
-}  // namespace ljh
+}  // namespace ljbh

@@ -1,0 +1,14 @@
+// lj_bh_mixed.cu -- bh_step_batched kernels, mixed-precision path.
+#include "lj_bh.cuh"
+
+namespace ljh {
+
+cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out) {
+  return ljbh::plan_impl<true>(n_atoms, m, n_walkers, K, team, out);
+}
+
+cudaError_t bh_launch_mixed(const BhArgs& a, const Plan& plan, cudaStream_t s) {
+  return ljbh::launch_impl<true>(a, plan, s);
+}
+
+}  // namespace ljh

@@ -28,13 +28,23 @@ struct Team {
   static_assert(T % 32 == 0 && T >= 32 && T <= 1024, "team size");
   int rank;       // 0 .. T-1
   int bar;        // named barrier id (T > 32); 1..15
-  double* red;    // shared scratch for cross-warp reductions: 8 * (T/32) doubles
+  double* red;    // shared scratch for cross-warp reductions: 2 x 8 x (T/32) doubles
+  mutable int flip = 0;   // which half of `red` the next reduction uses
   __device__ __forceinline__ void sync() const {
     if constexpr (T == 32) {
       __syncwarp();
     } else {
       asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(T) : "memory");
     }
+  }
+  // Scratch half for the next cross-warp reduction.  Alternating halves
+  // makes a barrier before the write unnecessary: a thread can only reach
+  // the reduction after next (same half) once every thread has passed the
+  // next reduction's barrier, i.e. has finished reading this one.
+  __device__ __forceinline__ double* scratch() const {
+    double* b = red + (flip ? 8 * (T / 32) : 0);
+    flip ^= 1;
+    return b;
   }
 };
 
@@ -54,8 +64,7 @@ __device__ __forceinline__ void team_sum(const Team<T>& tm, V (&v)[NV]) {
   if constexpr (T > 32) {
     static_assert(NV * sizeof(V) <= 8 * sizeof(double), "reduction scratch");
     constexpr int NW = T / 32;
-    V* buf = reinterpret_cast<V*>(tm.red);
-    tm.sync();
+    V* buf = reinterpret_cast<V*>(tm.scratch());
     if ((tm.rank & 31) == 0) {
 #pragma unroll
       for (int k = 0; k < NV; ++k) buf[(tm.rank >> 5) * NV + k] = v[k];
@@ -88,8 +97,7 @@ __device__ __forceinline__ void team_max(const Team<T>& tm, V (&v)[NV]) {
   }
   if constexpr (T > 32) {
     constexpr int NW = T / 32;
-    V* buf = reinterpret_cast<V*>(tm.red);
-    tm.sync();
+    V* buf = reinterpret_cast<V*>(tm.scratch());
     if ((tm.rank & 31) == 0) {
 #pragma unroll
       for (int k = 0; k < NV; ++k) buf[(tm.rank >> 5) * NV + k] = v[k];
@@ -160,8 +168,7 @@ __device__ __forceinline__ ff team_sum_ff(const Team<T>& tm, ff v) {
   }
   if constexpr (T > 32) {
     constexpr int NW = T / 32;
-    float* buf = reinterpret_cast<float*>(tm.red);
-    tm.sync();
+    float* buf = reinterpret_cast<float*>(tm.scratch());
     if ((tm.rank & 31) == 0) {
       buf[2 * (tm.rank >> 5)] = v.hi;
       buf[2 * (tm.rank >> 5) + 1] = v.lo;
@@ -297,8 +304,7 @@ __device__ __forceinline__ double team_sum_dd(const Team<T>& tm, dd v) {
   }
   if constexpr (T > 32) {
     constexpr int NW = T / 32;
-    double* buf = tm.red;
-    tm.sync();
+    double* buf = tm.scratch();
     if ((tm.rank & 31) == 0) {
       buf[2 * (tm.rank >> 5)] = v.hi;
       buf[2 * (tm.rank >> 5) + 1] = v.lo;

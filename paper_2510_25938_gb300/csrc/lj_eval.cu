@@ -1,9 +1,11 @@
-// lj_eval.cu -- batched Eq. (1) energy + gradient (lj_energy_grad_batched).
+// lj_eval.cu -- lj_energy_grad_batched: batched Eq. (1) energy + gradient.
 //
-// One team per candidate (a warp for N <= 64), teams stride over the batch.
-// The candidate's coordinates are loaded from HBM once, staged in shared
-// memory, and every thread sums the pair terms of its own atoms (one-sided
-// form: deterministic, no atomics).
+// Uniform batches (2..512 atoms): flat layout, one thread per atom, several
+// whole candidates per 1024-thread CTA.  Uneven batches: one team per
+// candidate (a warp for N <= 64), teams stride over the batch.  Either way
+// a candidate's coordinates are read from HBM once, staged in shared memory,
+// and every thread sums the pair terms of its own atom(s) (one-sided form:
+// deterministic, no atomics).
 #include "lj_internal.h"
 #include "lj_minimize.cuh"
 #include "lj_teams.cuh"
@@ -23,8 +25,9 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
   void* pos;
   long long* word;
   void* hbuf;
-  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, false), a.max_n, false, pos, hbuf,
-                tm.red, word);
+  void* hist;
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, false), a.max_n, false, 0, pos, hbuf,
+                hist, tm.red, word);
   MinParams p{};
   p.eps = a.eps;
   p.sigma = a.sigma;
@@ -69,6 +72,100 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
   }
 }
 
+// Flat layout for uniform batches: one thread per atom, C = floor(1024 / N)
+// whole candidates per CTA (for N = 38, 26 candidates = 988 of 1024 threads
+// busy), candidates' positions staged in shared memory, each thread summing
+// the pair terms of its own atom over its candidate (one-sided, no atomics),
+// per-candidate energies summed in fixed order from shared memory.
+template <typename X, typename IO>
+__global__ void __launch_bounds__(1024) eval_flat_kernel(ljh::EvalArgs a, int C) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using P = typename PosOf<X>::type;
+  using F = typename Tr<X>::F;
+  const int n = a.uniform_n;
+  P* pos = reinterpret_cast<P*>(smem);
+  F* esum = reinterpret_cast<F*>(smem + align16((size_t)C * n * sizeof(P)));
+  const int tid = threadIdx.x;
+  const int lc = tid / n;              // candidate within the CTA
+  const int i = tid - lc * n;          // atom within the candidate
+  const bool active = lc < C;
+  const X sig2 = (X)(a.sigma * a.sigma);
+  const X gscale = (X)(24.0 * a.eps / (a.sigma * a.sigma));
+  const IO* __restrict__ xin = static_cast<const IO*>(a.x);
+  IO* __restrict__ gout = static_cast<IO*>(a.grad);
+  for (long long c0 = (long long)blockIdx.x * C; c0 < a.n_cand; c0 += (long long)gridDim.x * C) {
+    const long long c = c0 + lc;
+    const bool live = active && c < a.n_cand;
+    const long long a0 = c * n;
+    X px = 0, py = 0, pz = 0;
+    if (live) {
+      px = (X)xin[3 * (a0 + i)];
+      py = (X)xin[3 * (a0 + i) + 1];
+      pz = (X)xin[3 * (a0 + i) + 2];
+      P q;
+      q.x = px; q.y = py; q.z = pz; q.w = (X)0;
+      pos[lc * n + i] = q;
+    }
+    __syncthreads();
+    if (live) {
+      X ax, ay, az;
+      F e;
+      if constexpr (sizeof(X) == 4) {
+        e = ff{0.f, 0.f};
+        pair_row_f32(n, i, px, py, pz, pos + lc * n, sig2, ax, ay, az, e);
+      } else {
+        dd ed{0.0, 0.0};
+        pair_row_f64(n, i, px, py, pz, pos + lc * n, sig2, ax, ay, az, ed);
+        e = ed.hi + ed.lo;
+      }
+      if (gout) {
+        gout[3 * (a0 + i)] = (IO)(-gscale * ax);
+        gout[3 * (a0 + i) + 1] = (IO)(-gscale * ay);
+        gout[3 * (a0 + i) + 2] = (IO)(-gscale * az);
+      }
+      esum[lc * n + i] = e;
+    }
+    __syncthreads();
+    if (live && i == 0) {
+      if constexpr (sizeof(X) == 4) {
+        ff t{0.f, 0.f};
+        for (int k = 0; k < n; ++k) t = ff_add(t, esum[lc * n + k]);
+        a.energy[c] = fto_double(t) * (2.0 * a.eps);
+      } else {
+        dd t{0.0, 0.0};
+        for (int k = 0; k < n; ++k) t = dd_add(t, dd{esum[lc * n + k], 0.0});
+        a.energy[c] = (t.hi + t.lo) * (2.0 * a.eps);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename X, typename IO>
+cudaError_t launch_flat(const ljh::EvalArgs& a, cudaStream_t s) {
+  using P = typename PosOf<X>::type;
+  const int n = a.uniform_n;
+  const int C = 1024 / n;
+  const size_t smem = align16((size_t)C * n * sizeof(P)) +
+                      (size_t)C * n * sizeof(typename Tr<X>::F);
+  auto k = eval_flat_kernel<X, IO>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 1024, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long need = (a.n_cand + C - 1) / C;
+  long long grid = (long long)per_sm * sms;
+  if (need < grid) grid = need;
+  k<<<(unsigned)grid, 1024, smem, s>>>(a, C);
+  return cudaGetLastError();
+}
+
 template <int T, int A, typename X, typename IO>
 cudaError_t launch_one(const ljh::EvalArgs& a, cudaStream_t s) {
   constexpr int threads = cta_threads_for(T);
@@ -97,6 +194,12 @@ cudaError_t launch_one(const ljh::EvalArgs& a, cudaStream_t s) {
 namespace ljh {
 
 cudaError_t eval_launch(const EvalArgs& a, cudaStream_t s) {
+  // uniform batches of 2..512 atoms: flat thread-per-atom layout
+  if (a.uniform_n >= 2 && a.uniform_n <= 512) {
+    const bool fp64 = a.prec == LJ_PREC_FP64;
+    if (a.xtype == LJ_F32) return fp64 ? launch_flat<double, float>(a, s) : launch_flat<float, float>(a, s);
+    return fp64 ? launch_flat<double, double>(a, s) : launch_flat<float, double>(a, s);
+  }
   return dispatch_team(a.max_n, [&](auto TT, auto AA) -> cudaError_t {
     constexpr int T = decltype(TT)::value;
     constexpr int A = decltype(AA)::value;

@@ -15,6 +15,7 @@ struct MinParamsH {     // mirror of ljd::MinParams (plain data)
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
   double eps, sigma;
+  double f32_resolution, df_resolution;   // handover thresholds, relative to |E|
 };
 
 struct EvalArgs {
@@ -46,6 +47,7 @@ struct LbfgsArgs {
   unsigned long long* queue;   // zeroed before the launch
   void* hist;
   size_t hist_slot_bytes;
+  int hist_on_chip;            // history in shared memory (hist unused)
 };
 
 struct BhArgs {
@@ -65,6 +67,7 @@ struct BhArgs {
   lj_stats* stats;
   void* hist;
   size_t hist_slot_bytes;
+  int hist_on_chip;            // history in shared memory (hist unused)
 };
 
 struct Plan {
@@ -75,15 +78,22 @@ struct Plan {
   int64_t slots;     // history slots the launch needs
   size_t slot_bytes; // bytes per history slot
   int cluster = 1;   // CTAs per thread-block cluster (Basin Hopping: K)
+  int hist_on_chip = 0;   // L-BFGS history in shared memory
 };
 
 // largest atom count this build supports
 constexpr int kMaxAtoms = LJ_MAX_ATOMS;
 
 cudaError_t eval_launch(const EvalArgs& a, cudaStream_t s);
-cudaError_t lbfgs_plan(int max_n, int m, int mixed, int64_t n_cand, int device, Plan* out);
-cudaError_t lbfgs_launch(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
-cudaError_t bh_plan(int n_atoms, int m, int mixed, int n_walkers, int K, Plan* out);
-cudaError_t bh_launch(const BhArgs& a, const Plan& plan, cudaStream_t s);
+// team: threads per candidate requested for clusters of up to 64 atoms
+// (32, 64 or 128); any other value picks the default for the cluster size.
+cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int team, Plan* out);
+cudaError_t lbfgs_plan_mixed(int max_n, int m, int64_t n_cand, int device, int team, Plan* out);
+cudaError_t lbfgs_launch_fp64(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t lbfgs_launch_mixed(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t bh_plan_fp64(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
+cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
+cudaError_t bh_launch_fp64(const BhArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t bh_launch_mixed(const BhArgs& a, const Plan& plan, cudaStream_t s);
 
 }  // namespace ljh

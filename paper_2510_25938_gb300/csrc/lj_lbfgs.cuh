@@ -1,14 +1,15 @@
-// lj_lbfgs.cu -- lbfgs_minimize_batched: a persistent kernel in which every
+// lj_lbfgs.cuh -- lbfgs_minimize_batched: a persistent kernel in which every
 // team takes candidates from a device work queue (one atomic counter) and
 // runs the whole L-BFGS loop on chip -- direction, line search, convergence
 // test -- with no host round trip per iteration.  Candidates converge after
 // different iteration counts; the queue keeps every team busy until the
 // batch is drained.
+#pragma once
 #include "lj_internal.h"
 #include "lj_minimize.cuh"
 #include "lj_teams.cuh"
 
-namespace {
+namespace ljlb {
 
 using namespace ljd;
 
@@ -17,6 +18,7 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
   p.m = h.m; p.max_iter = h.max_iter; p.max_ls = h.max_ls;
   p.gtol = h.gtol; p.c1 = h.c1; p.c2 = h.c2; p.alpha_max = h.alpha_max;
   p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.eps = h.eps; p.sigma = h.sigma;
+  p.f32_resolution = h.f32_resolution; p.df_resolution = h.df_resolution;
   return p;
 }
 
@@ -31,11 +33,13 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
   void* pos;
   long long* word;
   void* hbuf;
-  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true), a.max_n, true, pos, hbuf,
-                tm.red, word);
+  void* hist;
+  const size_t hb = a.hist_on_chip ? a.hist_slot_bytes : 0;
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true, hb), a.max_n, true, hb, pos,
+                hbuf, hist, tm.red, word);
   const MinParams p = to_dev(a.p);
   const long long slot = (long long)blockIdx.x * TPC + team;
-  void* hist = static_cast<unsigned char*>(a.hist) + slot * a.hist_slot_bytes;
+  if (!a.hist_on_chip) hist = static_cast<unsigned char*>(a.hist) + slot * a.hist_slot_bytes;
 
   for (;;) {
     long long c;
@@ -107,6 +111,8 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
         atomicAdd(&a.stats->cycles32, (unsigned long long)r.cyc32);
         atomicAdd(&a.stats->cycles_df, (unsigned long long)r.cycdf);
         atomicAdd(&a.stats->cycles64, (unsigned long long)r.cyc64);
+        atomicAdd(&a.stats->cycles_direction, (unsigned long long)r.cycdir);
+        atomicAdd(&a.stats->cycles_linesearch, (unsigned long long)r.cycls);
       }
     }
   }
@@ -116,7 +122,9 @@ template <int T, int A, bool MIXED>
 cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out) {
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
-  const size_t smem = TPC * team_smem_bytes<T>(max_n, true);
+  const size_t hist_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
+  const bool on_chip = TPC * team_smem_bytes<T>(max_n, true, hist_bytes) <= kSmemBudget;
+  const size_t smem = TPC * team_smem_bytes<T>(max_n, true, on_chip ? hist_bytes : 0);
   auto k = lbfgs_kernel<T, A, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -133,38 +141,43 @@ cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* ou
   out->teams_per_cta = TPC;
   out->grid = (int)grid;
   out->smem = smem;
-  out->slots = grid * TPC;
-  out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
+  out->slots = on_chip ? 0 : grid * TPC;
+  out->slot_bytes = hist_bytes;
+  out->hist_on_chip = on_chip ? 1 : 0;
   return cudaSuccess;
 }
 
-}  // namespace
+}  // namespace ljlb
 
-namespace ljh {
+namespace ljlb {
 
-cudaError_t lbfgs_plan(int max_n, int m, int mixed, int64_t n_cand, int device, Plan* out) {
-  return dispatch_team(max_n, [&](auto TT, auto AA) -> cudaError_t {
-    constexpr int T = decltype(TT)::value;
-    constexpr int A = decltype(AA)::value;
-    return mixed ? plan_one<T, A, true>(max_n, m, n_cand, device, out)
-                 : plan_one<T, A, false>(max_n, m, n_cand, device, out);
+// Team size: the default by cluster size, or the team chosen with
+// LJ_OPT_LBFGS_TEAM (32 / 64 / 128 threads) for clusters of up to 64 atoms.
+template <class F>
+cudaError_t dispatch_lb(int max_n, int team, F&& f) {
+  using std::integral_constant;
+  if (max_n <= 64 && team == 64) return f(integral_constant<int, 64>{}, integral_constant<int, 1>{});
+  if (max_n <= 64 && team == 128) return f(integral_constant<int, 128>{}, integral_constant<int, 1>{});
+  return dispatch_team(max_n, f);
+}
+
+template <bool MIXED>
+cudaError_t plan_impl(int max_n, int m, int64_t n_cand, int device, int team, ljh::Plan* out) {
+  return dispatch_lb(max_n, team, [&](auto TT, auto AA) -> cudaError_t {
+    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(max_n, m, n_cand, device, out);
   });
 }
 
-cudaError_t lbfgs_launch(const LbfgsArgs& a, const Plan& plan, cudaStream_t s) {
+template <bool MIXED>
+cudaError_t launch_impl(const ljh::LbfgsArgs& a, const ljh::Plan& plan, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  return dispatch_team(a.max_n, [&](auto TT, auto AA) -> cudaError_t {
+  return dispatch_lb(a.max_n, plan.team, [&](auto TT, auto AA) -> cudaError_t {
     constexpr int T = decltype(TT)::value;
     constexpr int A = decltype(AA)::value;
-    const int threads = cta_threads_for(T);
-    if (a.mixed) {
-      lbfgs_kernel<T, A, true><<<plan.grid, threads, plan.smem, s>>>(a);
-    } else {
-      lbfgs_kernel<T, A, false><<<plan.grid, threads, plan.smem, s>>>(a);
-    }
+    lbfgs_kernel<T, A, MIXED><<<plan.grid, cta_threads_for(T), plan.smem, s>>>(a);
     return cudaGetLastError();
   });
 }
 
-}  // namespace ljh
+}  // namespace ljlb

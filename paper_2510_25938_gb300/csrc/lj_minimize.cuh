@@ -26,7 +26,7 @@
 //               in FP64, pair terms in double-float arithmetic (FP32 pipes,
 //               ~1e-14 relative); directions and history stay FP32 (they only
 //               steer).  It hands over once the predicted decrease falls
-//               below the double-float energy resolution (~256 * 2^-48 |E|).
+//               below the double-float energy resolution (~32 * 2^-48 |E|).
 //               phase 3: FP64 pair terms for the last iterations; the
 //               convergence test and the returned energy are always FP64.
 #pragma once
@@ -40,6 +40,8 @@ struct MinParams {
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
   double eps, sigma;
+  double f32_resolution;   // FP32 phase hands over below this predicted decrease / |E|
+  double df_resolution;    // double-float polish hands over below this / |E|
 };
 
 struct MinResult {
@@ -49,6 +51,7 @@ struct MinResult {
   int evals32, evals64, evals_df, iters32, iters64;
   long long vec32, vec64;   // sum over iterations of (history used) * 3N
   long long cyc32, cycdf, cyc64;   // SM clock cycles spent in each tier
+  long long cycdir, cycls;          // ... in direction computations and line searches
 };
 
 enum : int { PH_CONVERGED = 0, PH_MAXITER = 1, PH_LSFAIL = 2, PH_SWITCH = 3, PH_TIMEOUT = 4 };
@@ -107,91 +110,113 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
   if constexpr (sizeof(X) == 8) {
     if (hbuf != nullptr) {
       // ---- half-pair evaluation ---------------------------------------------
+      // pair phase: thread `rank` takes pairs rank, rank + T, ...; two pairs
+      // per iteration (the second one clamped to a valid pair and discarded
+      // past the end) keep two independent dependency chains in flight.
+      // sum phase: one (atom, component) row sum per thread, written over the
+      // position buffer (no longer needed), then read back by the owners.
       const int np = n_pairs(n);
-      int i, j;
-      pair_start(n, tm.rank, i, j);
+      int i1, j1, i2, j2;
+      pair_start(n, tm.rank, i1, j1);
+      i2 = i1; j2 = j1;
+      pair_advance(n, T, i2, j2);
+      double* gsum = static_cast<double*>(posv);
       if constexpr (PM == 1) {
         const PosDF* pos = static_cast<const PosDF*>(posv);
         ff* vb = static_cast<ff*>(hbuf);
         ff e{0.f, 0.f};
-        for (int q = tm.rank; q < np; q += T) {
-          ff vx, vy, vz, ep;
-          pair_term_df(pos[i], pos[j], vx, vy, vz, ep);
-          vb[q] = vx; vb[np + q] = vy; vb[2 * np + q] = vz;
-          e = df_add(e, ep);
-          pair_advance(n, T, i, j);
+        for (int q = tm.rank; q < np; q += 2 * T) {
+          const bool two = q + T < np;
+          const int ib = two ? i2 : 0, jb = two ? j2 : 1;
+          ff ax, ay, az, ae, bx, by, bz, be;
+          pair_term_df(pos[i1], pos[j1], ax, ay, az, ae);
+          pair_term_df(pos[ib], pos[jb], bx, by, bz, be);
+          vb[q] = ax; vb[np + q] = ay; vb[2 * np + q] = az;
+          e = df_add(e, ae);
+          if (two) {
+            vb[q + T] = bx; vb[np + q + T] = by; vb[2 * np + q + T] = bz;
+            e = df_add(e, be);
+          }
+          pair_advance(n, 2 * T, i1, j1);
+          pair_advance(n, 2 * T, i2, j2);
         }
         tm.sync();
         const double gs = 24.0 * p.eps / p.sigma;
-#pragma unroll
-        for (int a = 0; a < A; ++a) {
-          const int ii = tm.rank + a * T;
-          if (ii < n) {
-            ff sx{0.f, 0.f}, sy{0.f, 0.f}, sz{0.f, 0.f};
-            for (int jj = 0; jj < n; ++jj) {
-              if (jj == ii) continue;
-              const int q = jj > ii ? pair_index(n, ii, jj) : pair_index(n, jj, ii);
-              ff vx = vb[q], vy = vb[np + q], vz = vb[2 * np + q];
-              if (jj < ii) {
-                vx = ff{-vx.hi, -vx.lo}; vy = ff{-vy.hi, -vy.lo}; vz = ff{-vz.hi, -vz.lo};
-              }
-              sx = df_add(sx, vx); sy = df_add(sy, vy); sz = df_add(sz, vz);
-            }
-            g[a][0] = -gs * df_to_double(sx);
-            g[a][1] = -gs * df_to_double(sy);
-            g[a][2] = -gs * df_to_double(sz);
-          } else {
-            g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+        for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
+          const int ii = q3 / 3;
+          const ff* vc = vb + (q3 - 3 * ii) * np;
+          ff s0{0.f, 0.f}, s1{0.f, 0.f};
+          int q = ii - 1;                       // pair (0, ii)
+          for (int jj = 0; jj < ii; ++jj) {     // -v over j < i
+            const ff v = vc[q];
+            if (jj & 1) s1 = df_sub(s1, v); else s0 = df_sub(s0, v);
+            q += n - jj - 2;
           }
-          if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+          q = pair_index(n, ii, ii + 1);
+          for (int jj = ii + 1; jj < n; ++jj, ++q) {   // +v over j > i
+            const ff v = vc[q];
+            if (jj & 1) s1 = df_add(s1, v); else s0 = df_add(s0, v);
+          }
+          gsum[q3] = -gs * df_to_double(df_add(s0, s1));
         }
-        E = team_sum_dd<T>(tm, dd_two_sum((double)e.hi, (double)e.lo)) * (4.0 * p.eps);
+        tm.sync();
+        // float-float team sum (FP32 pipes): its ~2^-47 relative error is far
+        // below the double-float handover resolution
+        E = fto_double(team_sum_ff<T>(tm, e)) * (4.0 * p.eps);
       } else {
         const PosD* pos = static_cast<const PosD*>(posv);
         double* vb = static_cast<double*>(hbuf);
         const double sig2 = p.sigma * p.sigma;
         dd e{0.0, 0.0};
-        double eb = 0.0;
-        int blk = 0;
-        for (int q = tm.rank; q < np; q += T) {
-          double vx, vy, vz, ep;
-          pair_term_f64(pos[i], pos[j], sig2, vx, vy, vz, ep);
-          vb[q] = vx; vb[np + q] = vy; vb[2 * np + q] = vz;
-          eb += ep;
-          if (++blk == 4) {           // fold 4-term blocks into the compensated sum
-            dd t = dd_two_sum(e.hi, eb);
-            e.hi = t.hi; e.lo = __dadd_rn(e.lo, t.lo);
-            eb = 0.0; blk = 0;
+        for (int q = tm.rank; q < np; q += 2 * T) {
+          const bool two = q + T < np;
+          const int ib = two ? i2 : 0, jb = two ? j2 : 1;
+          double ax, ay, az, ae, bx, by, bz, be;
+          pair_term_f64(pos[i1], pos[j1], sig2, ax, ay, az, ae);
+          pair_term_f64(pos[ib], pos[jb], sig2, bx, by, bz, be);
+          vb[q] = ax; vb[np + q] = ay; vb[2 * np + q] = az;
+          double eb = ae;
+          if (two) {
+            vb[q + T] = bx; vb[np + q + T] = by; vb[2 * np + q + T] = bz;
+            eb += be;
           }
-          pair_advance(n, T, i, j);
-        }
-        {
-          dd t = dd_two_sum(e.hi, eb);
-          e.hi = t.hi; e.lo = __dadd_rn(e.lo, t.lo);
+          const dd t = dd_two_sum(e.hi, eb);    // compensated energy sum
+          e.hi = t.hi;
+          e.lo = __dadd_rn(e.lo, t.lo);
+          pair_advance(n, 2 * T, i1, j1);
+          pair_advance(n, 2 * T, i2, j2);
         }
         tm.sync();
         const double gs = 24.0 * p.eps / sig2;
-#pragma unroll
-        for (int a = 0; a < A; ++a) {
-          const int ii = tm.rank + a * T;
-          if (ii < n) {
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int jj = 0; jj < n; ++jj) {
-              if (jj == ii) continue;
-              const int q = jj > ii ? pair_index(n, ii, jj) : pair_index(n, jj, ii);
-              const double sgn = jj > ii ? 1.0 : -1.0;
-              sx = fma(sgn, vb[q], sx); sy = fma(sgn, vb[np + q], sy); sz = fma(sgn, vb[2 * np + q], sz);
-            }
-            g[a][0] = -gs * sx; g[a][1] = -gs * sy; g[a][2] = -gs * sz;
-          } else {
-            g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+        for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
+          const int ii = q3 / 3;
+          const double* vc = vb + (q3 - 3 * ii) * np;
+          double s0 = 0.0, s1 = 0.0;
+          int q = ii - 1;
+          for (int jj = 0; jj < ii; ++jj) {
+            if (jj & 1) s1 -= vc[q]; else s0 -= vc[q];
+            q += n - jj - 2;
           }
-          if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+          q = pair_index(n, ii, ii + 1);
+          for (int jj = ii + 1; jj < n; ++jj, ++q) {
+            if (jj & 1) s1 += vc[q]; else s0 += vc[q];
+          }
+          gsum[q3] = -gs * (s0 + s1);
         }
+        tm.sync();
         E = team_sum_dd<T>(tm, e) * (4.0 * p.eps);
       }
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int ii = tm.rank + a * T;
+        if (ii < n) {
+          g[a][0] = gsum[3 * ii]; g[a][1] = gsum[3 * ii + 1]; g[a][2] = gsum[3 * ii + 2];
+        } else {
+          g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+        }
+        if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+      }
       if (d) dphi = (S)team_sum1<T, V>(tm, dp);
-      tm.sync();   // the buffer is reused by the next evaluation
       return;
     }
   }
@@ -199,7 +224,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
     static_assert(sizeof(X) == 8, "double-float pairs work on FP64 coordinates");
     const PosDF* pos = static_cast<const PosDF*>(posv);
     const double gs = 24.0 * p.eps / p.sigma;
-    dd e{0.0, 0.0};
+    ff e{0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int i = tm.rank + a * T;
@@ -210,13 +235,13 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
         g[a][0] = -gs * df_to_double(ax);
         g[a][1] = -gs * df_to_double(ay);
         g[a][2] = -gs * df_to_double(az);
-        e = dd_add(e, dd_two_sum((double)ea.hi, (double)ea.lo));
+        e = df_add(e, ea);
       } else {
         g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
       }
       if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
     }
-    E = team_sum_dd<T>(tm, e) * (2.0 * p.eps);
+    E = fto_double(team_sum_ff<T>(tm, e)) * (2.0 * p.eps);
   } else if constexpr (sizeof(X) == 4) {
     const PosF* pos = static_cast<const PosF*>(posv);
     ff e{0.f, 0.f};
@@ -310,31 +335,32 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 // MODE 0 (FP64, final): stops on ||g||_inf < gtol (CONVERGED) or a failed
 //   line search (LSFAIL).
 // MODE 1 (mixed, FP32 phase): hands over (SWITCH) once ||g||_inf <
-//   switch_gtol, once the predicted decrease -alpha phi'(0) is below ~8 ulp
-//   of the FP32 energy, or when a line search fails; never converges.
+//   switch_gtol, once the predicted decrease -alpha phi'(0) is below
+//   f32_resolution |E| (default 4 FP32 ulps), or when a line search fails;
+//   never converges.
 // MODE 2 (mixed, double-float polish): CONVERGED on ||g||_inf < gtol (to be
 //   confirmed in FP64); hands over to FP64 once the predicted decrease is
-//   below the double-float energy resolution, or when a line search fails.
+//   below df_resolution |E| (default 32 * 2^-48), or when a line search
+//   fails.
 // ---------------------------------------------------------------------------
-constexpr double kDfResolution = 256.0 * 3.552713678800501e-15;  // 256 * 2^-48, relative to |E|
-
 template <int T, int A, typename X, typename V, int MODE, int PM = 0>
 __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
                          typename Tr<X>::F& f, V* __restrict__ Sh, V* __restrict__ Yh,
                          V (&sy)[LJ_MAX_M], V (&yy)[LJ_MAX_M], int& cnt, int& head, int& iters,
                          int& evals, int& phase_iters, long long& vec, void* pos,
-                         void* hbuf, const MinParams& p, long long t0) {
+                         void* hbuf, const MinParams& p, long long t0, long long (&cyc)[2]) {
   using S = typename Tr<X>::S;
   using F = typename Tr<X>::F;
   const int m = p.m;
   const S c1 = (S)p.c1, c2 = (S)p.c2, amax = (S)p.alpha_max;
+  const S resolution = (S)(MODE == 1 ? p.f32_resolution : p.df_resolution);
   const X stop_gtol = MODE == 1 ? (X)p.switch_gtol : (X)p.gtol;
   V alpha[LJ_MAX_M];
   V d[A][3];
   X xt[A][3], gt[A][3];
-
   while (iters < p.max_iter) {
     // ---- search direction -------------------------------------------------
+    long long tc = clock64();
     S dphi0 = (S)1;
     if (cnt > 0) {
       V q[A][3];
@@ -342,43 +368,81 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
       for (int a = 0; a < A; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) q[a][c] = (V)g[a][c];
+      // two-loop recursion; each step prefetches the next pair's vectors and
+      // 1/s.y before its own team reduction, so loads overlap the reduction
+      auto slot_of = [&](int t) { const int sl = head + t; return sl >= m ? sl - m : sl; };
+      V sc[A][3], yc[A][3], sn[A][3], yn[A][3];
+      {
+        const int sl = slot_of(cnt - 1);
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sc[a][c] = Sh[hidx<T, A>(sl, a, c, tm.rank)];
+            yc[a][c] = Yh[hidx<T, A>(sl, a, c, tm.rank)];
+          }
+      }
+      V rho_c = (V)1 / sy[slot_of(cnt - 1)];
       for (int t = cnt - 1; t >= 0; --t) {
-        int slot = head + t;
-        if (slot >= m) slot -= m;
+        const int nsl = slot_of(t > 0 ? t - 1 : 0);
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sn[a][c] = Sh[hidx<T, A>(nsl, a, c, tm.rank)];
+            yn[a][c] = Yh[hidx<T, A>(nsl, a, c, tm.rank)];
+          }
+        const V rho_n = (V)1 / sy[nsl];
         V part = (V)0;
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) part += Sh[hidx<T, A>(slot, a, c, tm.rank)] * q[a][c];
-        const V rho = (V)1 / sy[slot];
-        const V al = rho * team_sum1<T, V>(tm, part);
+          for (int c = 0; c < 3; ++c) part += sc[a][c] * q[a][c];
+        const V al = rho_c * team_sum1<T, V>(tm, part);
         alpha[t] = al;
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) q[a][c] -= al * Yh[hidx<T, A>(slot, a, c, tm.rank)];
+          for (int c = 0; c < 3; ++c) {
+            q[a][c] -= al * yc[a][c];
+            sc[a][c] = sn[a][c];
+            yc[a][c] = yn[a][c];
+          }
+        rho_c = rho_n;
       }
-      int newest = head + cnt - 1;
-      if (newest >= m) newest -= m;
+      const int newest = slot_of(cnt - 1);
       const V gam = sy[newest] / yy[newest];
 #pragma unroll
       for (int a = 0; a < A; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) q[a][c] *= gam;
+      // (sc, yc) now hold the oldest pair, the first one of the second loop
+      rho_c = (V)1 / sy[slot_of(0)];
       for (int t = 0; t < cnt; ++t) {
-        int slot = head + t;
-        if (slot >= m) slot -= m;
+        const int nsl = slot_of(t + 1 < cnt ? t + 1 : t);
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sn[a][c] = Sh[hidx<T, A>(nsl, a, c, tm.rank)];
+            yn[a][c] = Yh[hidx<T, A>(nsl, a, c, tm.rank)];
+          }
+        const V rho_n = (V)1 / sy[nsl];
         V part = (V)0;
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) part += Yh[hidx<T, A>(slot, a, c, tm.rank)] * q[a][c];
-        const V rho = (V)1 / sy[slot];
-        const V coef = alpha[t] - rho * team_sum1<T, V>(tm, part);
+          for (int c = 0; c < 3; ++c) part += yc[a][c] * q[a][c];
+        const V coef = alpha[t] - rho_c * team_sum1<T, V>(tm, part);
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) q[a][c] += coef * Sh[hidx<T, A>(slot, a, c, tm.rank)];
+          for (int c = 0; c < 3; ++c) {
+            q[a][c] += coef * sc[a][c];
+            sc[a][c] = sn[a][c];
+            yc[a][c] = yn[a][c];
+          }
+        rho_c = rho_n;
       }
       V part = (V)0;
 #pragma unroll
@@ -406,6 +470,11 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
     }
     bool ok = false;
     F ft;
+    {
+      const long long t1 = clock64();
+      cyc[0] += t1 - tc;
+      tc = t1;
+    }
     for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
       if (attempt == 1) {
         if (cnt == 0) break;  // already steepest descent: no retry
@@ -427,11 +496,11 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         if (a1 > (S)1) a1 = (S)1;
       }
       if constexpr (MODE == 1) {
-        // predicted decrease below ~8 ulp of the FP32 energy: hand over
-        if (-dphi0 * a1 < (S)4.76837158203125e-7 * fabsf(f.hi)) return PH_SWITCH;
+        // predicted decrease below the FP32 energy resolution: hand over
+        if (-dphi0 * a1 < resolution * fabsf(f.hi)) return PH_SWITCH;
       } else if constexpr (MODE == 2) {
         // predicted decrease below the double-float energy resolution
-        if (-dphi0 * a1 < (S)kDfResolution * fabs(f)) return PH_SWITCH;
+        if (-dphi0 * a1 < resolution * fabs(f)) return PH_SWITCH;
       }
       // ---- strong-Wolfe line search ----------------------------------------
       int ev = 0;
@@ -513,6 +582,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
       evals += ev;
       ok = done;
     }
+    cyc[1] += clock64() - tc;
     if (!ok) return MODE == 0 ? PH_LSFAIL : PH_SWITCH;
 
     // ---- curvature pair, then move ------------------------------------------
@@ -594,7 +664,8 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
   r.E = 0.0; r.status = ST_CONVERGED; r.iters = 0;
   r.evals32 = 0; r.evals64 = 0; r.evals_df = 0; r.iters32 = 0; r.iters64 = 0;
   r.vec32 = 0; r.vec64 = 0;
-  r.cyc32 = 0; r.cycdf = 0; r.cyc64 = 0;
+  r.cyc32 = 0; r.cycdf = 0; r.cyc64 = 0; r.cycdir = 0; r.cycls = 0;
+  long long cyc[2] = {0, 0};
   if (n <= 1) return;
   const long long t0 = clock64();
   long long tmark = t0;
@@ -602,6 +673,8 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
     const long long t = clock64();
     acc += t - tmark;
     tmark = t;
+    r.cycdir = cyc[0];
+    r.cycls = cyc[1];
   };
   int cnt = 0, head = 0, iters = 0;
   const size_t hstride = (size_t)p.m * A * 3 * T;
@@ -620,7 +693,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
     double* Sh = (double*)hist;
     const int code = run_phase<T, A, double, double, 0>(
         tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt, head, iters, r.evals64, r.iters64,
-        r.vec64, pos, hbuf, p, t0);
+        r.vec64, pos, hbuf, p, t0, cyc);
     r.E = f;
     r.iters = iters;
     r.status = status_of(code);
@@ -645,7 +718,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
         code = run_phase<T, A, float, float, 1>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt, head,
                                                 iters, r.evals32, r.iters32, r.vec32, pos, nullptr,
-                                                p, t0);
+                                                p, t0, cyc);
         if (r.iters32 > 0) {
 #pragma unroll
           for (int a = 0; a < A; ++a)
@@ -676,7 +749,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         }
         code = run_phase<T, A, double, float, 2, 1>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
                                                      iters, r.evals_df, r.iters64, r.vec64, pos,
-                                                     hbuf, p, t0);
+                                                     hbuf, p, t0, cyc);
         if (code == PH_CONVERGED) {
           gm = 0.0;
         } else if (code == PH_SWITCH) {
@@ -699,8 +772,8 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
         r.E = f; r.iters = iters; r.status = ST_CONVERGED; lap(r.cyc64); return;
       }
       code = run_phase<T, A, double, float, 0>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
-                                               iters, r.evals64, r.iters64, r.vec64, pos, hbuf, p,
-                                               t0);
+                                               iters, r.evals64, r.iters64, r.vec64, pos, hbuf,
+                                               p, t0, cyc);
       r.E = f;
       r.iters = iters;
       r.status = status_of(code);

@@ -33,25 +33,32 @@ __host__ __device__ constexpr size_t half_bytes(int max_n, bool half) {
 }
 
 // per-team shared bytes: positions (32-byte records; the FP32 phase uses the
-// first half of the same buffer), the optional half-pair buffer, cross-warp
-// reduction scratch, one word
+// first half of the same buffer), the optional half-pair buffer, the optional
+// L-BFGS history (hist_bytes > 0: kept on chip instead of in the workspace),
+// cross-warp reduction scratch (double-buffered), one word
 template <int T>
-__host__ __device__ constexpr size_t team_smem_bytes(int max_n, bool half) {
-  return align16((size_t)max_n * sizeof(PosD)) + half_bytes(max_n, half) +
-         (T > 32 ? 8 * (T / 32) * sizeof(double) : 0) + 16;
+__host__ __device__ constexpr size_t team_smem_bytes(int max_n, bool half, size_t hist_bytes = 0) {
+  return align16((size_t)max_n * sizeof(PosD)) + half_bytes(max_n, half) + align16(hist_bytes) +
+         (T > 32 ? 2 * 8 * (T / 32) * sizeof(double) : 0) + 16;
 }
 
 template <int T>
-__device__ __forceinline__ void carve_team(unsigned char* base, int max_n, bool half, void*& pos,
-                                           void*& hbuf, double*& red, long long*& word) {
+__device__ __forceinline__ void carve_team(unsigned char* base, int max_n, bool half,
+                                           size_t hist_bytes, void*& pos, void*& hbuf,
+                                           void*& hist, double*& red, long long*& word) {
   pos = base;
   unsigned char* p = base + align16((size_t)max_n * sizeof(PosD));
   const size_t hb = half_bytes(max_n, half);
   hbuf = hb ? static_cast<void*>(p) : nullptr;
   p += hb;
+  hist = hist_bytes ? static_cast<void*>(p) : nullptr;
+  p += align16(hist_bytes);
   red = reinterpret_cast<double*>(p);
-  p += (T > 32 ? 8 * (T / 32) * sizeof(double) : 0);
+  p += (T > 32 ? 2 * 8 * (T / 32) * sizeof(double) : 0);
   word = reinterpret_cast<long long*>(p);
 }
+
+// History goes on chip when a CTA's shared memory stays within this budget.
+constexpr size_t kSmemBudget = 100 * 1024;
 
 }  // namespace ljd

@@ -24,9 +24,10 @@ LJ_PREC_FP64, LJ_PREC_FP32, LJ_PREC_MIXED = 0, 1, 2
 (LJ_CAND_CONVERGED, LJ_CAND_MAXITER, LJ_CAND_LINESEARCH_FAIL, LJ_CAND_NONFINITE,
  LJ_CAND_TIMEOUT, LJ_CAND_BAD_INPUT) = range(6)
 LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 16
+LJ_OPT_BH_TEAM, LJ_OPT_LBFGS_TEAM, LJ_OPT_F32_HANDOVER, LJ_OPT_DF_HANDOVER = 1, 2, 3, 4
 STATS_FIELDS = ("evals32", "evals64", "evals_df", "iters32", "iters64", "pairs32", "pairs64",
                 "pairs_df", "vec_elems32", "vec_elems64", "converged", "minimisations",
-                "cycles32", "cycles_df", "cycles64")
+                "cycles32", "cycles_df", "cycles64", "cycles_direction", "cycles_linesearch")
 
 
 class LjError(RuntimeError):
@@ -93,6 +94,8 @@ def load():
             lib.lj_ctx_destroy.restype = C.c_int
             lib.lj_ctx_reserve.argtypes = [P, C.c_int64, C.c_int32, C.c_int32]
             lib.lj_ctx_reserve.restype = C.c_int
+            lib.lj_ctx_set_option.argtypes = [P, C.c_int, C.c_int64]
+            lib.lj_ctx_set_option.restype = C.c_int
             lib.lj_ctx_last_error.argtypes = [P]
             lib.lj_ctx_last_error.restype = C.c_char_p
             lib.lj_energy_grad_batched.argtypes = [P, C.POINTER(_Batch), C.c_int, C.c_int, P, P,
@@ -148,6 +151,10 @@ class Ctx:
 
     def reserve(self, max_cand: int, max_n: int, max_m: int):
         _check(self, load().lj_ctx_reserve(self.handle, max_cand, max_n, max_m), "lj_ctx_reserve")
+
+    def set_option(self, opt: int, value: int):
+        """lj_ctx_set_option: e.g. set_option(LJ_OPT_BH_TEAM, 64)."""
+        _check(self, load().lj_ctx_set_option(self.handle, opt, value), "lj_ctx_set_option")
 
     def close(self):
         if getattr(self, "handle", None):
