@@ -242,6 +242,45 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
 lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_params* p,
                           const lj_bh_trace* trace, lj_stats* d_stats, void* stream);
 
+/*
+ * lbfgs_minimize_batched_noalloc -- the same minimisation as
+ * lbfgs_minimize_batched, for callers that must not allocate device memory.
+ * (Not part of the method: the paper has no counterpart; it only changes
+ * where this library keeps its scratch memory.)
+ *
+ * Who needs it: code that records the call into a CUDA graph (cudaMalloc may
+ * synchronise the device, which stream capture forbids), applications whose
+ * memory manager has already reserved the device memory and does not allow
+ * further cudaMalloc/cudaFree, and latency-critical loops that cannot pay for
+ * an allocation.  It takes no lj_ctx (creating one allocates) and uses the
+ * default tuning options.
+ *
+ * Scratch: a fixed array of LJ_NOALLOC_SCRATCH_BYTES in the library's
+ * device-global memory holds the work-queue counter and any L-BFGS history
+ * that does not fit in shared memory.  Every GPU that loads the library
+ * holds this array until the process exits.  When the history of all teams
+ * would not fit, fewer teams are launched (each still drains the shared work
+ * queue), so a large batch takes longer but still runs; a batch whose
+ * smallest launch (one CTA) would not fit returns LJ_ERR_NO_WORKSPACE.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Later calls use the cached address.
+ *
+ * Calls share the array: the counter is cleared at the start of every call
+ * and the previous call's contents are otherwise left in place.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on it; order
+ * them on one stream.
+ *
+ * Arguments, results and errors are those of lbfgs_minimize_batched; the
+ * call runs on the device that is current for the calling host thread.
+ */
+#define LJ_NOALLOC_SCRATCH_BYTES (16u << 20)
+lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_params* p,
+                                         double* d_x, double* d_energy, int32_t* d_status,
+                                         int32_t* d_iters, int32_t* d_nevals, lj_stats* d_stats,
+                                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

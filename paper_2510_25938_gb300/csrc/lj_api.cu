@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <cuda_runtime.h>
@@ -132,6 +133,30 @@ ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p) {
   h.switch_gtol = p->switch_gtol; h.deadline = p->deadline_cycles;
   h.eps = p->eps; h.sigma = p->sigma;
   return h;
+}
+
+// ---- scratch of lbfgs_minimize_batched_noalloc ----------------------------
+// The array lives in device-global memory of every GPU that loads this
+// library.  Host code must not use its name as an address: the address is
+// looked up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LJ_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr size_t kNoallocQueueBytes = 256;   // work-queue counter, padded
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// device address of the scratch array on `dev` (current device), set up once
+lj_status noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return LJ_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LJ_ERR_CUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LJ_OK;
 }
 
 }  // namespace
@@ -363,6 +388,62 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
             : ljh::bh_launch_fp64(a, plan, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "bh_step_batched launch");
   return LJ_OK;
+}
+
+lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_params* p,
+                                         double* d_x, double* d_energy, int32_t* d_status,
+                                         int32_t* d_iters, int32_t* d_nevals, lj_stats* d_stats,
+                                         void* stream) {
+  int max_n = 0;
+  lj_status st = check_batch(nullptr, batch, &max_n);
+  if (st != LJ_OK) return st;
+  st = check_min(nullptr, p);
+  if (st != LJ_OK) return st;
+  if (batch->n_cand == 0) return LJ_OK;
+  if (!d_x || !d_energy) return LJ_ERR_INVALID_ARG;
+  if (!aligned(d_x, 8) || !aligned(d_energy, 8) || (d_status && !aligned(d_status, 4)) ||
+      (d_iters && !aligned(d_iters, 4)) || (d_nevals && !aligned(d_nevals, 4)) ||
+      (d_stats && !aligned(d_stats, 8)))
+    return LJ_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LJ_ERR_CUDA;
+  void* scratch = nullptr;
+  st = noalloc_scratch(dev, &scratch);
+  if (st != LJ_OK) return st;
+  const int mixed = p->prec == LJ_PREC_MIXED;
+  ljh::Plan plan;
+  cudaError_t e = mixed ? ljh::lbfgs_plan_mixed(max_n, p->m, batch->n_cand, dev, 0, &plan)
+                        : ljh::lbfgs_plan_fp64(max_n, p->m, batch->n_cand, dev, 0, &plan);
+  if (e != cudaSuccess) return LJ_ERR_CUDA;
+  if (!plan.hist_on_chip) {
+    // launch only as many teams as the scratch holds history slots for
+    const size_t avail = LJ_NOALLOC_SCRATCH_BYTES - kNoallocQueueBytes;
+    const int64_t cap = (int64_t)(avail / plan.slot_bytes) / plan.teams_per_cta;
+    if (cap < 1) return LJ_ERR_NO_WORKSPACE;
+    if (plan.grid > cap) plan.grid = (int)cap;
+    plan.slots = (int64_t)plan.grid * plan.teams_per_cta;
+  }
+  static const lj_ctx kDefaults;       // default tuning options
+  ljh::LbfgsArgs a;
+  a.n_cand = batch->n_cand;
+  a.uniform_n = batch->uniform_n;
+  a.off = batch->d_atom_offset;
+  a.max_n = max_n;
+  a.p = to_host(&kDefaults, p);
+  a.mixed = mixed;
+  a.x = d_x;
+  a.energy = d_energy;
+  a.status = d_status;
+  a.iters = d_iters;
+  a.nevals = d_nevals;
+  a.stats = d_stats;
+  a.queue = static_cast<unsigned long long*>(scratch);
+  a.hist = static_cast<unsigned char*>(scratch) + kNoallocQueueBytes;
+  a.hist_slot_bytes = plan.slot_bytes;
+  a.hist_on_chip = plan.hist_on_chip;
+  e = mixed ? ljh::lbfgs_launch_mixed(a, plan, (cudaStream_t)stream)
+            : ljh::lbfgs_launch_fp64(a, plan, (cudaStream_t)stream);
+  return e == cudaSuccess ? LJ_OK : LJ_ERR_CUDA;
 }
 
 }  // extern "C"

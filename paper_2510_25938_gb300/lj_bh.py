@@ -107,6 +107,9 @@ def load():
             lib.bh_step_batched.argtypes = [P, C.POINTER(_State), C.POINTER(_Bh),
                                             C.POINTER(_Trace), P, P]
             lib.bh_step_batched.restype = C.c_int
+            lib.lbfgs_minimize_batched_noalloc.argtypes = [C.POINTER(_Batch), C.POINTER(_Lbfgs),
+                                                           P, P, P, P, P, P, P]
+            lib.lbfgs_minimize_batched_noalloc.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -265,6 +268,29 @@ def lbfgs_minimize_batched(ctx: Ctx, x: torch.Tensor, energy: torch.Tensor,
                                        _ptr(status), _ptr(iters), _ptr(nevals), _ptr(stats),
                                        _stream(stream))
     _check(ctx, st, "lbfgs_minimize_batched")
+
+
+def lbfgs_minimize_batched_noalloc(x: torch.Tensor, energy: torch.Tensor,
+                                   status: torch.Tensor | None = None,
+                                   iters: torch.Tensor | None = None,
+                                   nevals: torch.Tensor | None = None,
+                                   stats: torch.Tensor | None = None, *, n_cand: int,
+                                   uniform_n: int = 0, atom_offset: torch.Tensor | None = None,
+                                   max_n: int = 0, params: LbfgsParams | None = None,
+                                   stream=None):
+    """lbfgs_minimize_batched without a context and without any device
+    allocation (scratch in a fixed library array; see include/lj_bh.h).
+    Runs on the current CUDA device."""
+    if x.dtype != torch.float64 or energy.dtype != torch.float64:
+        raise ValueError("x and energy must be float64")
+    p = (params or LbfgsParams()).c()
+    b = _batch(n_cand, uniform_n, atom_offset, max_n)
+    st = load().lbfgs_minimize_batched_noalloc(C.byref(b), C.byref(p), _ptr(x), _ptr(energy),
+                                               _ptr(status), _ptr(iters), _ptr(nevals),
+                                               _ptr(stats), _stream(stream))
+    if st != LJ_OK:
+        raise LjError(st, "lbfgs_minimize_batched_noalloc: "
+                          + load().lj_status_string(st).decode())
 
 
 STATE_KEYS = (("x_cur", torch.float64), ("e_cur", torch.float64), ("x_best", torch.float64),
