@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
     }
     typename Tr<X>::F E;
     typename Tr<X>::S dummy;
-    evaluate<T, A, X, X>(tm, n, x, g, pos, nullptr, p, nullptr, E, dummy);
+    evaluate<T, A, Prec<X, X, X, 0>>(tm, n, x, g, pos, nullptr, p, nullptr, E, dummy);
     if (gout) {
 #pragma unroll
       for (int s = 0; s < A; ++s) {

@@ -22,14 +22,18 @@
 //               FP64 instruction at all; it ends when ||g32||_inf <
 //               switch_gtol, when the predicted decrease falls below the FP32
 //               energy resolution, or when its line search fails.
-//               phase 2 (polish): coordinates, gradient and energy carried
-//               in FP64, pair terms in double-float arithmetic (FP32 pipes,
-//               ~1e-14 relative); directions and history stay FP32 (they only
-//               steer).  It hands over once the predicted decrease falls
-//               below the double-float energy resolution (~32 * 2^-48 |E|).
-//               phase 3: FP64 pair terms for the last iterations; the
+//               phase 2 (polish): coordinates and pair terms in double-float
+//               arithmetic (FP32 pipes, ~1e-14 relative), gradient FP32
+//               (only its relative precision is used there), energies
+//               float-float, line-search scalars FP32: no FP64 instruction.
+//               It hands over once the predicted decrease falls below the
+//               double-float energy resolution (~32 * 2^-48 |E|).
+//               phase 3: FP64 coordinates, gradient, energy and pair terms
+//               for the last iterations (FP32 directions and scalars); the
 //               convergence test and the returned energy are always FP64.
 #pragma once
+#include <type_traits>
+
 #include "lj_device.cuh"
 #include "../../include/lj_bh.h"
 
@@ -56,9 +60,45 @@ struct MinResult {
 
 enum : int { PH_CONVERGED = 0, PH_MAXITER = 1, PH_LSFAIL = 2, PH_SWITCH = 3, PH_TIMEOUT = 4 };
 
+// Precision policy of an L-BFGS tier.
+//   XP positions (float, double, or ff = double-float), XG gradient, V search
+//   directions and history, PM pair arithmetic (0: XP's own, 1: double-float).
+//   S line-search scalars: FP64 only on the all-FP64 path.  F energies: FP64
+//   when positions are FP64, float-float otherwise (FP32 pipes only).
+template <typename XP_, typename XG_, typename V_, int PM_>
+struct Prec {
+  using XP = XP_;
+  using XG = XG_;
+  using V = V_;
+  static constexpr int PM = PM_;
+  using S = std::conditional_t<sizeof(V_) == 8, double, float>;
+  using F = std::conditional_t<std::is_same<XP_, double>::value, double, ff>;
+};
+using PrecF32 = Prec<float, float, float, 0>;      // mixed: FP32 tier
+using PrecDF = Prec<ff, float, float, 1>;          // mixed: double-float tier
+using PrecF64m = Prec<double, double, float, 0>;   // mixed: FP64 tier
+using PrecF64 = Prec<double, double, double, 0>;   // FP64 path
+
+// Eval-only helper: scalars of a plain single-precision evaluation.
 template <typename X> struct Tr;
 template <> struct Tr<float> { using S = float; using F = ff; };
 template <> struct Tr<double> { using S = double; using F = double; };
+
+// trial position x + a d and step xt - x for each position type
+__device__ __forceinline__ float pos_step(float x, float a, float d) { return x + a * d; }
+template <typename SA, typename VD>
+__device__ __forceinline__ double pos_step(double x, SA a, VD d) {
+  return x + (double)a * (double)d;
+}
+__device__ __forceinline__ ff pos_step(ff x, float a, float d) {
+  return df_add(x, df_two_prod(a, d));
+}
+template <typename V> __device__ __forceinline__ V pos_diff(float xt, float x) { return (V)(xt - x); }
+template <typename V> __device__ __forceinline__ V pos_diff(double xt, double x) { return (V)(xt - x); }
+template <typename V> __device__ __forceinline__ V pos_diff(ff xt, ff x) {
+  const ff d = df_sub(xt, x);
+  return (V)(d.hi + d.lo);
+}
 
 template <typename V> __device__ __forceinline__ V eps_mach();
 template <> __device__ __forceinline__ float eps_mach<float>() { return 1.1920928955078125e-7f; }
@@ -80,23 +120,32 @@ __device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
 // double-float arithmetic on coordinates scaled by 1/sigma.
 // hbuf: the team's half-pair buffer (24 bytes per pair) or nullptr; used for
 // FP64 / double-float evaluations, which then compute each pair once.
-template <int T, int A, typename X, typename V, int PM = 0>
-__device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[A][3], X (&g)[A][3],
-                                         void* posv, void* hbuf, const MinParams& p,
-                                         const V (*d)[3], typename Tr<X>::F& E,
-                                         typename Tr<X>::S& dphi) {
-  using S = typename Tr<X>::S;
-  const X sig2 = (X)(p.sigma * p.sigma);
-  const X gscale = (X)(24.0 * p.eps / (p.sigma * p.sigma));
+template <int T, int A, typename P>
+__device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
+                                         const typename P::XP (&x)[A][3],
+                                         typename P::XG (&g)[A][3], void* posv, void* hbuf,
+                                         const MinParams& p, const typename P::V (*d)[3],
+                                         typename P::F& E, typename P::S& dphi) {
+  using X = typename P::XP;
+  using XG = typename P::XG;
+  using V = typename P::V;
+  using S = typename P::S;
+  constexpr int PM = P::PM;
+  using XR = std::conditional_t<std::is_same<X, float>::value, float, double>;   // pair-term real
+  const XR sig2 = (XR)(p.sigma * p.sigma);
+  const XR gscale = (XR)(24.0 * p.eps / (p.sigma * p.sigma));
   tm.sync();  // previous readers of pos are done
 #pragma unroll
   for (int a = 0; a < A; ++a) {
     const int i = tm.rank + a * T;
     if (i < n) {
       if constexpr (PM == 1) {
-        const double is = 1.0 / p.sigma;
-        const ff qx = df_from_double(x[a][0] * is), qy = df_from_double(x[a][1] * is),
-                 qz = df_from_double(x[a][2] * is);
+        // double-float positions, scaled by 1/sigma (exact for sigma = 1)
+        ff qx = x[a][0], qy = x[a][1], qz = x[a][2];
+        if (p.sigma != 1.0) {
+          const ff is = df_from_double(1.0 / p.sigma);
+          qx = df_mul(qx, is); qy = df_mul(qy, is); qz = df_mul(qz, is);
+        }
         static_cast<PosDF*>(posv)[i] = PosDF{qx.hi, qy.hi, qz.hi, 0.f, qx.lo, qy.lo, qz.lo, 0.f};
       } else {
         typename PosOf<X>::type q;
@@ -107,7 +156,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
   }
   tm.sync();
   V dp = (V)0;
-  if constexpr (sizeof(X) == 8) {
+  if constexpr (PM == 1 || std::is_same<X, double>::value) {
     if (hbuf != nullptr) {
       // ---- half-pair evaluation ---------------------------------------------
       // pair phase: thread `rank` takes pairs rank, rank + T, ...; two pairs
@@ -120,7 +169,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
       pair_start(n, tm.rank, i1, j1);
       i2 = i1; j2 = j1;
       pair_advance(n, T, i2, j2);
-      double* gsum = static_cast<double*>(posv);
+      XG* gsum = static_cast<XG*>(posv);
       if constexpr (PM == 1) {
         const PosDF* pos = static_cast<const PosDF*>(posv);
         ff* vb = static_cast<ff*>(hbuf);
@@ -141,7 +190,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
           pair_advance(n, 2 * T, i2, j2);
         }
         tm.sync();
-        const double gs = 24.0 * p.eps / p.sigma;
+        const float gs = (float)(24.0 * p.eps / p.sigma);
         for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
           const int ii = q3 / 3;
           const ff* vc = vb + (q3 - 3 * ii) * np;
@@ -157,12 +206,13 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
             const ff v = vc[q];
             if (jj & 1) s1 = df_add(s1, v); else s0 = df_add(s0, v);
           }
-          gsum[q3] = -gs * df_to_double(df_add(s0, s1));
+          const ff sum = df_add(s0, s1);
+          gsum[q3] = -gs * (sum.hi + sum.lo);
         }
         tm.sync();
         // float-float team sum (FP32 pipes): its ~2^-47 relative error is far
         // below the double-float handover resolution
-        E = fto_double(team_sum_ff<T>(tm, e)) * (4.0 * p.eps);
+        E = ff_scale(team_sum_ff<T>(tm, e), (float)(4.0 * p.eps));
       } else {
         const PosD* pos = static_cast<const PosD*>(posv);
         double* vb = static_cast<double*>(hbuf);
@@ -221,9 +271,8 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
     }
   }
   if constexpr (PM == 1) {
-    static_assert(sizeof(X) == 8, "double-float pairs work on FP64 coordinates");
     const PosDF* pos = static_cast<const PosDF*>(posv);
-    const double gs = 24.0 * p.eps / p.sigma;
+    const float gs = (float)(24.0 * p.eps / p.sigma);
     ff e{0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
@@ -232,16 +281,16 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n, const X (&x)[
         const PosDF q = pos[i];
         ff ax, ay, az, ea{0.f, 0.f};
         pair_row_df(n, i, ff{q.xh, q.xl}, ff{q.yh, q.yl}, ff{q.zh, q.zl}, pos, ax, ay, az, ea);
-        g[a][0] = -gs * df_to_double(ax);
-        g[a][1] = -gs * df_to_double(ay);
-        g[a][2] = -gs * df_to_double(az);
+        g[a][0] = -gs * (ax.hi + ax.lo);
+        g[a][1] = -gs * (ay.hi + ay.lo);
+        g[a][2] = -gs * (az.hi + az.lo);
         e = df_add(e, ea);
       } else {
-        g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+        g[a][0] = (XG)0; g[a][1] = (XG)0; g[a][2] = (XG)0;
       }
       if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
     }
-    E = fto_double(team_sum_ff<T>(tm, e)) * (2.0 * p.eps);
+    E = ff_scale(team_sum_ff<T>(tm, e), (float)(2.0 * p.eps));
   } else if constexpr (sizeof(X) == 4) {
     const PosF* pos = static_cast<const PosF*>(posv);
     ff e{0.f, 0.f};
@@ -343,21 +392,27 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 //   below df_resolution |E| (default 32 * 2^-48), or when a line search
 //   fails.
 // ---------------------------------------------------------------------------
-template <int T, int A, typename X, typename V, int MODE, int PM = 0>
-__device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
-                         typename Tr<X>::F& f, V* __restrict__ Sh, V* __restrict__ Yh,
-                         V (&sy)[LJ_MAX_M], V (&yy)[LJ_MAX_M], int& cnt, int& head, int& iters,
+template <int T, int A, typename P, int MODE>
+__device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
+                         typename P::XG (&g)[A][3], typename P::F& f,
+                         typename P::V* __restrict__ Sh, typename P::V* __restrict__ Yh,
+                         typename P::V (&sy)[LJ_MAX_M], typename P::V (&yy)[LJ_MAX_M], int& cnt,
+                         int& head, int& iters,
                          int& evals, int& phase_iters, long long& vec, void* pos,
                          void* hbuf, const MinParams& p, long long t0, long long (&cyc)[2]) {
-  using S = typename Tr<X>::S;
-  using F = typename Tr<X>::F;
+  using X = typename P::XP;
+  using XG = typename P::XG;
+  using V = typename P::V;
+  using S = typename P::S;
+  using F = typename P::F;
   const int m = p.m;
   const S c1 = (S)p.c1, c2 = (S)p.c2, amax = (S)p.alpha_max;
   const S resolution = (S)(MODE == 1 ? p.f32_resolution : p.df_resolution);
-  const X stop_gtol = MODE == 1 ? (X)p.switch_gtol : (X)p.gtol;
+  const XG stop_gtol = MODE == 1 ? (XG)p.switch_gtol : (XG)p.gtol;
   V alpha[LJ_MAX_M];
   V d[A][3];
-  X xt[A][3], gt[A][3];
+  X xt[A][3];
+  XG gt[A][3];
   while (iters < p.max_iter) {
     // ---- search direction -------------------------------------------------
     long long tc = clock64();
@@ -495,12 +550,9 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
         a1 = (S)1 / S_sqrt(-dphi0);
         if (a1 > (S)1) a1 = (S)1;
       }
-      if constexpr (MODE == 1) {
-        // predicted decrease below the FP32 energy resolution: hand over
+      if constexpr (MODE == 1 || MODE == 2) {
+        // predicted decrease below this tier's energy resolution: hand over
         if (-dphi0 * a1 < resolution * fabsf(f.hi)) return PH_SWITCH;
-      } else if constexpr (MODE == 2) {
-        // predicted decrease below the double-float energy resolution
-        if (-dphi0 * a1 < resolution * fabs(f)) return PH_SWITCH;
       }
       // ---- strong-Wolfe line search ----------------------------------------
       int ev = 0;
@@ -518,8 +570,8 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
 #pragma unroll
         for (int aa = 0; aa < A; ++aa)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) xt[aa][c] = x[aa][c] + (X)al * (X)d[aa][c];
-        evaluate<T, A, X, V, PM>(tm, n, xt, gt, pos, hbuf, p, d, fo, dpo);
+          for (int c = 0; c < 3; ++c) xt[aa][c] = pos_step(x[aa][c], al, d[aa][c]);
+        evaluate<T, A, P>(tm, n, xt, gt, pos, hbuf, p, d, fo, dpo);
         ++ev;
         last_a = al;
       };
@@ -592,7 +644,7 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
     for (int a = 0; a < A; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        sv[a][c] = (V)(xt[a][c] - x[a][c]);
+        sv[a][c] = pos_diff<V>(xt[a][c], x[a][c]);
         yv[a][c] = (V)(gt[a][c] - g[a][c]);
         pr[0] += sv[a][c] * yv[a][c];
         pr[1] += yv[a][c] * yv[a][c];
@@ -629,16 +681,16 @@ __device__ int run_phase(const Team<T>& tm, int n, X (&x)[A][3], X (&g)[A][3],
     ++iters;
     ++phase_iters;
     // ---- stopping tests ----------------------------------------------------
-    X mv[2];
-    mv[0] = (X)0;
+    XG mv[2];
+    mv[0] = (XG)0;
 #pragma unroll
     for (int a = 0; a < A; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) mv[0] = fmax(mv[0], abs_nan_inf(g[a][c]));
-    mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (X)1 : (X)0;
-    team_max<T, 2, X>(tm, mv);
+    mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (XG)1 : (XG)0;
+    team_max<T, 2, XG>(tm, mv);
     if (mv[0] < stop_gtol) return MODE == 1 ? PH_SWITCH : PH_CONVERGED;
-    if (mv[1] > (X)0) return PH_TIMEOUT;
+    if (mv[1] > (XG)0) return PH_TIMEOUT;
   }
   return PH_MAXITER;
 }
@@ -682,18 +734,18 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
   if constexpr (!MIXED) {
     double g[A][3];
     double f, dummy;
-    evaluate<T, A, double, double>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
+    evaluate<T, A, PrecF64>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
     r.evals64 = 1;
     const double gm = grad_max<T, A, double>(tm, g);
     if (!isfinite(f) || !(gm < kInf)) {
-      r.E = f; r.status = ST_NONFINITE; return;
+      r.E = f; r.status = ST_NONFINITE; lap(r.cyc64); return;
     }
-    if (gm < p.gtol) { r.E = f; return; }
+    if (gm < p.gtol) { r.E = f; lap(r.cyc64); return; }
     double sy[LJ_MAX_M], yy[LJ_MAX_M];
     double* Sh = (double*)hist;
-    const int code = run_phase<T, A, double, double, 0>(
-        tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt, head, iters, r.evals64, r.iters64,
-        r.vec64, pos, hbuf, p, t0, cyc);
+    const int code = run_phase<T, A, PrecF64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt,
+                                                 head, iters, r.evals64, r.iters64, r.vec64, pos,
+                                                 hbuf, p, t0, cyc);
     r.E = f;
     r.iters = iters;
     r.status = status_of(code);
@@ -703,66 +755,78 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
     float* Yh = Sh + hstride;
     float sy[LJ_MAX_M], yy[LJ_MAX_M];
     int code = PH_SWITCH;
-    // ---- tier 1: FP32 -----------------------------------------------------
+    float dummy32;
+    // ---- tier 1: FP32 -------------------------------------------------------
+    float x32[A][3];
+    bool moved32 = false;
     {
-      float x32[A][3], g32[A][3];
+      float g32[A][3];
 #pragma unroll
       for (int a = 0; a < A; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) x32[a][c] = (float)x64[a][c];
       ff f32;
-      float dummy;
-      evaluate<T, A, float, float>(tm, n, x32, g32, pos, nullptr, p, nullptr, f32, dummy);
+      evaluate<T, A, PrecF32>(tm, n, x32, g32, pos, nullptr, p, nullptr, f32, dummy32);
       r.evals32 = 1;
       const float gm = grad_max<T, A, float>(tm, g32);
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
-        code = run_phase<T, A, float, float, 1>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt, head,
-                                                iters, r.evals32, r.iters32, r.vec32, pos, nullptr,
-                                                p, t0, cyc);
-        if (r.iters32 > 0) {
-#pragma unroll
-          for (int a = 0; a < A; ++a)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
-        }
+        code = run_phase<T, A, PrecF32, 1>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt, head,
+                                           iters, r.evals32, r.iters32, r.vec32, pos, nullptr, p,
+                                           t0, cyc);
+        moved32 = r.iters32 > 0;
       }
     }
     lap(r.cyc32);
-    double g[A][3];
-    double f, dummy;
     int status = -1;
     bool need_fp64 = false;
     if (code == PH_MAXITER || code == PH_TIMEOUT) {
       status = status_of(code);
-    } else {
-      // ---- tier 2: double-float polish --------------------------------------
-      evaluate<T, A, double, double, 1>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
-      r.evals_df += 1;
-      double gm = grad_max<T, A, double>(tm, g);
-      if (!isfinite(f) || !(gm < kInf)) {
-        need_fp64 = true;                 // let FP64 judge the point
+      if (moved32) {
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
       }
+    } else {
+      // ---- tier 2: double-float positions and pair terms, FP32 elsewhere -----
+      ff xdf[A][3];
+      float gdf[A][3];
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          xdf[a][c] = moved32 ? ff{x32[a][c], 0.f} : df_from_double(x64[a][c]);
+      ff fdf;
+      evaluate<T, A, PrecDF>(tm, n, xdf, gdf, pos, hbuf, p, nullptr, fdf, dummy32);
+      r.evals_df += 1;
+      float gm = grad_max<T, A, float>(tm, gdf);
+      if (!fisfinite(fdf) || !(gm < __int_as_float(0x7f800000))) need_fp64 = true;
       while (status < 0 && !need_fp64) {
-        if (gm < p.gtol) {
+        if (gm < (float)p.gtol) {
           need_fp64 = true;               // confirm (and finish) in FP64
           break;
         }
-        code = run_phase<T, A, double, float, 2, 1>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
-                                                     iters, r.evals_df, r.iters64, r.vec64, pos,
-                                                     hbuf, p, t0, cyc);
+        code = run_phase<T, A, PrecDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, sy, yy, cnt, head, iters,
+                                          r.evals_df, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
         if (code == PH_CONVERGED) {
-          gm = 0.0;
+          gm = 0.f;
         } else if (code == PH_SWITCH) {
           need_fp64 = true;
         } else {
           status = status_of(code);
         }
       }
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x64[a][c] = (double)xdf[a][c].hi + (double)xdf[a][c].lo;
     }
     lap(r.cycdf);
+    double g[A][3];
+    double f, dummy;
     if (need_fp64) {
       // ---- tier 3: FP64 -------------------------------------------------------
-      evaluate<T, A, double, double>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
+      evaluate<T, A, PrecF64m>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy32);
       r.evals64 += 1;
       const double gm = grad_max<T, A, double>(tm, g);
       if (!isfinite(f) || !(gm < kInf)) {
@@ -771,9 +835,8 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       if (gm < p.gtol) {
         r.E = f; r.iters = iters; r.status = ST_CONVERGED; lap(r.cyc64); return;
       }
-      code = run_phase<T, A, double, float, 0>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head,
-                                               iters, r.evals64, r.iters64, r.vec64, pos, hbuf,
-                                               p, t0, cyc);
+      code = run_phase<T, A, PrecF64m, 0>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head, iters,
+                                          r.evals64, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
       r.E = f;
       r.iters = iters;
       r.status = status_of(code);
@@ -781,7 +844,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       return;
     }
     // final energy (and the non-finite test) in FP64
-    evaluate<T, A, double, double>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
+    evaluate<T, A, PrecF64>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
     r.evals64 += 1;
     const double gm = grad_max<T, A, double>(tm, g);
     r.E = f;
