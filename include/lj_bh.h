@@ -256,12 +256,14 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_par
  * default tuning options.
  *
  * Scratch: a fixed array of LJ_NOALLOC_SCRATCH_BYTES in the library's
- * device-global memory holds the work-queue counter and any L-BFGS history
- * that does not fit in shared memory.  Every GPU that loads the library
- * holds this array until the process exits.  When the history of all teams
- * would not fit, fewer teams are launched (each still drains the shared work
- * queue), so a large batch takes longer but still runs; a batch whose
- * smallest launch (one CTA) would not fit returns LJ_ERR_NO_WORKSPACE.
+ * device-global memory holds the work-queue counters, the size-bucket lists
+ * of an uneven batch (6 x 4 bytes per candidate) and any L-BFGS history that
+ * does not fit in shared memory.  Every GPU that loads the library holds
+ * this array until the process exits.  When the history of all teams would
+ * not fit, fewer teams are launched (each still drains the shared work
+ * queue), so a large batch takes longer but still runs.  A batch whose
+ * bucket lists, or whose smallest launch (one CTA), would not fit returns
+ * LJ_ERR_NO_WORKSPACE (an uneven batch of more than ~690,000 candidates).
  *
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call

@@ -1,5 +1,6 @@
 // lj_api.cu -- the C ABI of include/lj_bh.h: context, workspace, argument
 // validation and kernel dispatch.  Host code only.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -17,6 +18,8 @@ struct lj_ctx {
   int sms = 0;
   void* ws = nullptr;                  // L-BFGS history workspace
   size_t ws_bytes = 0;
+  void* aux = nullptr;                 // bucket lists / counters of uneven batches
+  size_t aux_bytes = 0;
   bool reserved = false;
   unsigned long long* queue = nullptr; // persistent-kernel work counter
   int bh_team = 0;                     // LJ_OPT_BH_TEAM (0 = automatic)
@@ -83,6 +86,29 @@ lj_status ensure_ws(lj_ctx* ctx, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace cudaMalloc");
   ctx->ws_bytes = bytes;
   return LJ_OK;
+}
+
+lj_status ensure_aux(lj_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->aux_bytes) return LJ_OK;
+  if (ctx->reserved) {
+    return fail(ctx, LJ_ERR_NO_WORKSPACE,
+                "call needs " + std::to_string(bytes) + " bucket-list bytes, reserved " +
+                    std::to_string(ctx->aux_bytes));
+  }
+  if (ctx->aux) {
+    cudaFree(ctx->aux);
+    ctx->aux = nullptr;
+    ctx->aux_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->aux, bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bucket-list cudaMalloc");
+  ctx->aux_bytes = bytes;
+  return LJ_OK;
+}
+
+// bytes of the bucket lists for n_cand candidates: counters, queues, lists
+size_t aux_bytes_for(int64_t n_cand) {
+  return 256 + (size_t)ljh::kMaxBuckets * (size_t)n_cand * sizeof(int);
 }
 
 lj_status check_batch(lj_ctx* ctx, const lj_batch* b, int* max_n) {
@@ -197,6 +223,7 @@ lj_status lj_ctx_destroy(lj_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->queue) cudaFree(ctx->queue);
   }
   delete ctx;
@@ -214,6 +241,8 @@ lj_status lj_ctx_reserve(lj_ctx* ctx, int64_t max_cand, int32_t max_n, int32_t m
   const size_t bytes = (size_t)slots * slot_bytes_bound(max_n < 1 ? 1 : max_n, max_m);
   ctx->reserved = false;
   lj_status st = ensure_ws(ctx, bytes);
+  if (st != LJ_OK) return st;
+  st = ensure_aux(ctx, aux_bytes_for(max_cand));
   if (st != LJ_OK) return st;
   ctx->reserved = true;
   return LJ_OK;
@@ -299,11 +328,67 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
   const int mixed = p->prec == LJ_PREC_MIXED;
+  auto plan_for = [&](int bound, ljh::Plan* pl) {
+    return mixed ? ljh::lbfgs_plan_mixed(bound, p->m, batch->n_cand, ctx->device,
+                                         ctx->lbfgs_team, pl)
+                 : ljh::lbfgs_plan_fp64(bound, p->m, batch->n_cand, ctx->device,
+                                        ctx->lbfgs_team, pl);
+  };
+  if (batch->uniform_n == 0 && max_n > 32 && batch->n_cand > 1) {
+    // Uneven batch spanning several size classes: sort candidates into size
+    // buckets on the device and drain each bucket with the team shape made
+    // for it (one persistent launch per bucket, counts never leave the GPU).
+    static const int kBound[ljh::kMaxBuckets] = {32, 64, 128, 256, 512, 1024};
+    int nb = 1;
+    while (nb < ljh::kMaxBuckets && kBound[nb - 1] < max_n) ++nb;
+    ljh::Buckets bk;
+    for (int b = 0; b < ljh::kMaxBuckets; ++b) bk.bound[b] = b < nb - 1 ? kBound[b] : max_n;
+    ljh::Plan plans[ljh::kMaxBuckets];
+    size_t hist_need = 0;
+    for (int b = 0; b < nb; ++b) {
+      cudaError_t e = plan_for(bk.bound[b], &plans[b]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched plan");
+      hist_need = std::max(hist_need, (size_t)plans[b].slots * plans[b].slot_bytes);
+    }
+    st = ensure_ws(ctx, hist_need);
+    if (st != LJ_OK) return st;
+    st = ensure_aux(ctx, aux_bytes_for(batch->n_cand));
+    if (st != LJ_OK) return st;
+    unsigned* counts = static_cast<unsigned*>(ctx->aux);
+    unsigned long long* queues = reinterpret_cast<unsigned long long*>(
+        static_cast<unsigned char*>(ctx->aux) + 128);
+    int* lists = reinterpret_cast<int*>(static_cast<unsigned char*>(ctx->aux) + 256);
+    cudaError_t e = ljh::bucketize_launch(batch->d_atom_offset, batch->n_cand, nb, bk, counts,
+                                          lists, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched bucketize");
+    for (int b = 0; b < nb; ++b) {
+      ljh::LbfgsArgs a;
+      a.n_cand = batch->n_cand;
+      a.uniform_n = 0;
+      a.off = batch->d_atom_offset;
+      a.max_n = bk.bound[b];
+      a.p = to_host(ctx, p);
+      a.mixed = mixed;
+      a.x = d_x;
+      a.energy = d_energy;
+      a.status = d_status;
+      a.iters = d_iters;
+      a.nevals = d_nevals;
+      a.stats = d_stats;
+      a.queue = queues + b;
+      a.hist = ctx->ws;
+      a.hist_slot_bytes = plans[b].slot_bytes;
+      a.hist_on_chip = plans[b].hist_on_chip;
+      a.list = lists + (size_t)b * batch->n_cand;
+      a.list_count = counts + b;
+      e = mixed ? ljh::lbfgs_launch_mixed(a, plans[b], (cudaStream_t)stream)
+                : ljh::lbfgs_launch_fp64(a, plans[b], (cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
+    }
+    return LJ_OK;
+  }
   ljh::Plan plan;
-  cudaError_t e = mixed ? ljh::lbfgs_plan_mixed(max_n, p->m, batch->n_cand, ctx->device,
-                                                ctx->lbfgs_team, &plan)
-                        : ljh::lbfgs_plan_fp64(max_n, p->m, batch->n_cand, ctx->device,
-                                               ctx->lbfgs_team, &plan);
+  cudaError_t e = plan_for(max_n, &plan);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched plan");
   st = ensure_ws(ctx, (size_t)plan.slots * plan.slot_bytes);
   if (st != LJ_OK) return st;
@@ -411,39 +496,75 @@ lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_p
   st = noalloc_scratch(dev, &scratch);
   if (st != LJ_OK) return st;
   const int mixed = p->prec == LJ_PREC_MIXED;
-  ljh::Plan plan;
-  cudaError_t e = mixed ? ljh::lbfgs_plan_mixed(max_n, p->m, batch->n_cand, dev, 0, &plan)
-                        : ljh::lbfgs_plan_fp64(max_n, p->m, batch->n_cand, dev, 0, &plan);
-  if (e != cudaSuccess) return LJ_ERR_CUDA;
-  if (!plan.hist_on_chip) {
-    // launch only as many teams as the scratch holds history slots for
-    const size_t avail = LJ_NOALLOC_SCRATCH_BYTES - kNoallocQueueBytes;
-    const int64_t cap = (int64_t)(avail / plan.slot_bytes) / plan.teams_per_cta;
-    if (cap < 1) return LJ_ERR_NO_WORKSPACE;
-    if (plan.grid > cap) plan.grid = (int)cap;
-    plan.slots = (int64_t)plan.grid * plan.teams_per_cta;
-  }
   static const lj_ctx kDefaults;       // default tuning options
-  ljh::LbfgsArgs a;
-  a.n_cand = batch->n_cand;
-  a.uniform_n = batch->uniform_n;
-  a.off = batch->d_atom_offset;
-  a.max_n = max_n;
-  a.p = to_host(&kDefaults, p);
-  a.mixed = mixed;
-  a.x = d_x;
-  a.energy = d_energy;
-  a.status = d_status;
-  a.iters = d_iters;
-  a.nevals = d_nevals;
-  a.stats = d_stats;
-  a.queue = static_cast<unsigned long long*>(scratch);
-  a.hist = static_cast<unsigned char*>(scratch) + kNoallocQueueBytes;
-  a.hist_slot_bytes = plan.slot_bytes;
-  a.hist_on_chip = plan.hist_on_chip;
-  e = mixed ? ljh::lbfgs_launch_mixed(a, plan, (cudaStream_t)stream)
-            : ljh::lbfgs_launch_fp64(a, plan, (cudaStream_t)stream);
-  return e == cudaSuccess ? LJ_OK : LJ_ERR_CUDA;
+  // scratch layout: [0, 128) work-queue counters, [128, 256) bucket counts,
+  // then the bucket lists (uneven batches), then off-chip history slots
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  unsigned long long* queues = reinterpret_cast<unsigned long long*>(base);
+  unsigned* counts = reinterpret_cast<unsigned*>(base + 128);
+  const bool bucketed = batch->uniform_n == 0 && max_n > 32 && batch->n_cand > 1;
+  const size_t list_bytes =
+      bucketed ? (((size_t)ljh::kMaxBuckets * (size_t)batch->n_cand * sizeof(int) + 255) & ~size_t(255))
+               : 0;
+  if (kNoallocQueueBytes + list_bytes > LJ_NOALLOC_SCRATCH_BYTES) return LJ_ERR_NO_WORKSPACE;
+  int* lists = reinterpret_cast<int*>(base + kNoallocQueueBytes);
+  unsigned char* hist = base + kNoallocQueueBytes + list_bytes;
+  const size_t avail = LJ_NOALLOC_SCRATCH_BYTES - kNoallocQueueBytes - list_bytes;
+  // same bucketing as lbfgs_minimize_batched, so both give the same results
+  static const int kBound[ljh::kMaxBuckets] = {32, 64, 128, 256, 512, 1024};
+  int nb = 1;
+  ljh::Buckets bk;
+  if (bucketed) {
+    while (nb < ljh::kMaxBuckets && kBound[nb - 1] < max_n) ++nb;
+    for (int b = 0; b < ljh::kMaxBuckets; ++b) bk.bound[b] = b < nb - 1 ? kBound[b] : max_n;
+  } else {
+    bk.bound[0] = max_n;
+  }
+  ljh::Plan plans[ljh::kMaxBuckets];
+  for (int b = 0; b < nb; ++b) {
+    cudaError_t e = mixed ? ljh::lbfgs_plan_mixed(bk.bound[b], p->m, batch->n_cand, dev, 0, &plans[b])
+                          : ljh::lbfgs_plan_fp64(bk.bound[b], p->m, batch->n_cand, dev, 0, &plans[b]);
+    if (e != cudaSuccess) return LJ_ERR_CUDA;
+    if (!plans[b].hist_on_chip) {
+      // launch only as many teams as the scratch holds history slots for
+      const int64_t cap = (int64_t)(avail / plans[b].slot_bytes) / plans[b].teams_per_cta;
+      if (cap < 1) return LJ_ERR_NO_WORKSPACE;
+      if (plans[b].grid > cap) plans[b].grid = (int)cap;
+      plans[b].slots = (int64_t)plans[b].grid * plans[b].teams_per_cta;
+    }
+  }
+  if (bucketed) {
+    cudaError_t e = ljh::bucketize_launch(batch->d_atom_offset, batch->n_cand, nb, bk, counts,
+                                          lists, (cudaStream_t)stream);
+    if (e != cudaSuccess) return LJ_ERR_CUDA;
+  }
+  for (int b = 0; b < nb; ++b) {
+    ljh::LbfgsArgs a;
+    a.n_cand = batch->n_cand;
+    a.uniform_n = batch->uniform_n;
+    a.off = batch->d_atom_offset;
+    a.max_n = bk.bound[b];
+    a.p = to_host(&kDefaults, p);
+    a.mixed = mixed;
+    a.x = d_x;
+    a.energy = d_energy;
+    a.status = d_status;
+    a.iters = d_iters;
+    a.nevals = d_nevals;
+    a.stats = d_stats;
+    a.queue = queues + b;
+    a.hist = hist;
+    a.hist_slot_bytes = plans[b].slot_bytes;
+    a.hist_on_chip = plans[b].hist_on_chip;
+    if (bucketed) {
+      a.list = lists + (size_t)b * batch->n_cand;
+      a.list_count = counts + b;
+    }
+    cudaError_t e = mixed ? ljh::lbfgs_launch_mixed(a, plans[b], (cudaStream_t)stream)
+                          : ljh::lbfgs_launch_fp64(a, plans[b], (cudaStream_t)stream);
+    if (e != cudaSuccess) return LJ_ERR_CUDA;
+  }
+  return LJ_OK;
 }
 
 }  // extern "C"

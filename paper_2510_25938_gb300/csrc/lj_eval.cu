@@ -1,7 +1,7 @@
 // lj_eval.cu -- lj_energy_grad_batched: batched Eq. (1) energy + gradient.
 //
 // Uniform batches (2..512 atoms): flat layout, one thread per atom, several
-// whole candidates per 1024-thread CTA.  Uneven batches: one team per
+// whole candidates per 512-thread CTA.  Uneven batches: one team per
 // candidate (a warp for N <= 64), teams stride over the batch.  Either way
 // a candidate's coordinates are read from HBM once, staged in shared memory,
 // and every thread sums the pair terms of its own atom(s) (one-sided form:
@@ -72,13 +72,22 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
   }
 }
 
-// Flat layout for uniform batches: one thread per atom, C = floor(1024 / N)
-// whole candidates per CTA (for N = 38, 26 candidates = 988 of 1024 threads
-// busy), candidates' positions staged in shared memory, each thread summing
-// the pair terms of its own atom over its candidate (one-sided, no atomics),
-// per-candidate energies summed in fixed order from shared memory.
+// Flat layout for uniform batches: one thread per atom, C = floor(512 / N)
+// whole candidates per 512-thread CTA (several CTAs per SM overlap each
+// other's barriers), candidates' positions staged in shared memory, each
+// thread summing the pair terms of its own atom over its candidate
+// (one-sided, no atomics), per-candidate energies summed by a fixed-order
+// shared-memory tree (log2 N steps).
+constexpr int kFlatThreads = 512;
+
+__host__ __device__ constexpr int pow2_ceil(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
 template <typename X, typename IO>
-__global__ void __launch_bounds__(1024) eval_flat_kernel(ljh::EvalArgs a, int C) {
+__global__ void __launch_bounds__(kFlatThreads) eval_flat_kernel(ljh::EvalArgs a, int C) {
   extern __shared__ __align__(16) unsigned char smem[];
   using P = typename PosOf<X>::type;
   using F = typename Tr<X>::F;
@@ -93,6 +102,7 @@ __global__ void __launch_bounds__(1024) eval_flat_kernel(ljh::EvalArgs a, int C)
   const X gscale = (X)(24.0 * a.eps / (a.sigma * a.sigma));
   const IO* __restrict__ xin = static_cast<const IO*>(a.x);
   IO* __restrict__ gout = static_cast<IO*>(a.grad);
+  const int top = pow2_ceil(n) >> 1;
   for (long long c0 = (long long)blockIdx.x * C; c0 < a.n_cand; c0 += (long long)gridDim.x * C) {
     const long long c = c0 + lc;
     const bool live = active && c < a.n_cand;
@@ -125,19 +135,20 @@ __global__ void __launch_bounds__(1024) eval_flat_kernel(ljh::EvalArgs a, int C)
       }
       esum[lc * n + i] = e;
     }
-    __syncthreads();
-    if (live && i == 0) {
-      if constexpr (sizeof(X) == 4) {
-        ff t{0.f, 0.f};
-        for (int k = 0; k < n; ++k) t = ff_add(t, esum[lc * n + k]);
-        a.energy[c] = fto_double(t) * (2.0 * a.eps);
-      } else {
-        dd t{0.0, 0.0};
-        for (int k = 0; k < n; ++k) t = dd_add(t, dd{esum[lc * n + k], 0.0});
-        a.energy[c] = (t.hi + t.lo) * (2.0 * a.eps);
+    // fixed-order tree over each candidate's n per-atom energies
+    for (int stride = top; stride > 0; stride >>= 1) {
+      __syncthreads();
+      if (live && i < stride && i + stride < n) {
+        F* ep = esum + lc * n;
+        if constexpr (sizeof(X) == 4) {
+          ep[i] = ff_add(ep[i], ep[i + stride]);
+        } else {
+          ep[i] = ep[i] + ep[i + stride];
+        }
       }
     }
     __syncthreads();
+    if (live && i == 0) a.energy[c] = fto_double(esum[lc * n]) * (2.0 * a.eps);
   }
 }
 
@@ -145,7 +156,7 @@ template <typename X, typename IO>
 cudaError_t launch_flat(const ljh::EvalArgs& a, cudaStream_t s) {
   using P = typename PosOf<X>::type;
   const int n = a.uniform_n;
-  const int C = 1024 / n;
+  const int C = kFlatThreads / n;
   const size_t smem = align16((size_t)C * n * sizeof(P)) +
                       (size_t)C * n * sizeof(typename Tr<X>::F);
   auto k = eval_flat_kernel<X, IO>;
@@ -156,13 +167,13 @@ cudaError_t launch_flat(const ljh::EvalArgs& a, cudaStream_t s) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 1024, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFlatThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long need = (a.n_cand + C - 1) / C;
   long long grid = (long long)per_sm * sms;
   if (need < grid) grid = need;
-  k<<<(unsigned)grid, 1024, smem, s>>>(a, C);
+  k<<<(unsigned)grid, kFlatThreads, smem, s>>>(a, C);
   return cudaGetLastError();
 }
 
@@ -195,7 +206,7 @@ namespace ljh {
 
 cudaError_t eval_launch(const EvalArgs& a, cudaStream_t s) {
   // uniform batches of 2..512 atoms: flat thread-per-atom layout
-  if (a.uniform_n >= 2 && a.uniform_n <= 512) {
+  if (a.uniform_n >= 2 && a.uniform_n <= kFlatThreads) {
     const bool fp64 = a.prec == LJ_PREC_FP64;
     if (a.xtype == LJ_F32) return fp64 ? launch_flat<double, float>(a, s) : launch_flat<float, float>(a, s);
     return fp64 ? launch_flat<double, double>(a, s) : launch_flat<float, double>(a, s);

@@ -48,6 +48,14 @@ struct LbfgsArgs {
   void* hist;
   size_t hist_slot_bytes;
   int hist_on_chip;            // history in shared memory (hist unused)
+  const int* list = nullptr;   // bucketed launch: candidate indices of this bucket
+  const unsigned* list_count = nullptr;   // ... and their number (device)
+};
+
+// size classes of a bucketed uneven batch (upper atom count per bucket)
+constexpr int kMaxBuckets = 6;
+struct Buckets {
+  int bound[kMaxBuckets];
 };
 
 struct BhArgs {
@@ -91,6 +99,9 @@ cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int te
 cudaError_t lbfgs_plan_mixed(int max_n, int m, int64_t n_cand, int device, int team, Plan* out);
 cudaError_t lbfgs_launch_fp64(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
 cudaError_t lbfgs_launch_mixed(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
+// sort candidates of an uneven batch into size buckets (device, no sync)
+cudaError_t bucketize_launch(const int64_t* off, int64_t n_cand, int nb, const Buckets& bk,
+                             unsigned* counts, int* lists, cudaStream_t s);
 cudaError_t bh_plan_fp64(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
 cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
 cudaError_t bh_launch_fp64(const BhArgs& a, const Plan& plan, cudaStream_t s);

@@ -53,7 +53,12 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
       c = *word;
       tm.sync();
     }
-    if (c >= a.n_cand) break;
+    if (a.list) {                         // bucketed launch: this bucket's candidates
+      if (c >= (long long)*a.list_count) break;
+      c = a.list[c];
+    } else if (c >= a.n_cand) {
+      break;
+    }
     long long a0;
     int n;
     if (a.uniform_n > 0) {
@@ -181,3 +186,4 @@ cudaError_t launch_impl(const ljh::LbfgsArgs& a, const ljh::Plan& plan, cudaStre
 }
 
 }  // namespace ljlb
+

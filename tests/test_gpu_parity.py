@@ -475,3 +475,27 @@ def test_invalid_arguments(lj, ctx):
     rc = lib.lj_energy_grad_batched(ctx.handle, C.byref(b), 0, lj.LJ_F64, x.data_ptr() + 4,
                                     e.data_ptr(), None, 1.0, 1.0, None)
     assert rc == lj.LJ_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------
+# full-size uneven batch (4,096 candidates, N uniform on 13..150, cube starts
+# at reduced density 0.3, mixed precision): every candidate valid, a sample
+# compared with the oracle
+# ---------------------------------------------------------------------------
+def test_uneven_4096_full_size_sampled(lj, ctx):
+    sizes = I.uneven_sizes(4096, 13, 150, I.workload_seed(3))
+    x0, off = I.uneven_cube_starts(sizes, 0.3, I.workload_seed(3) + 1)
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, off=off, prec=2)
+    assert stats["minimisations"] == 4096
+    assert (sg == O.CONVERGED).mean() >= 0.95
+    assert np.all(np.isin(sg, [O.CONVERGED, O.LINESEARCH_FAIL]))
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(4096, 24, replace=False))
+    sub_sizes = sizes[sample]
+    sub_off = I.offsets_from_sizes(sub_sizes)
+    x_sub = np.concatenate([x0[3 * off[c]:3 * off[c + 1]] for c in sample])
+    xo, eo, so, _, _ = O.lbfgs_batch(x_sub, sample.size, atom_off=sub_off)
+    xg_sub = np.concatenate([xg[3 * off[c]:3 * off[c + 1]] for c in sample])
+    # cube starts: chaotic; validity for all, same-basin energy match where it occurs
+    _compare_minima(x_sub, sub_off, xg_sub, eg[sample], sg[sample], xo, eo, so,
+                    MIX_ABS_FINAL, 0.0, 0.0)
