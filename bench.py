@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true", help="skip the evaluation microbench")
+    ap.add_argument("--micro-only", action="store_true",
+                    help="run only the evaluation microbench and print its JSON")
+    ap.add_argument("--micro-repeats", type=int, default=100)
     ap.add_argument("--profile", action="store_true",
                     help="mixed-precision steps only (no FP64 arm, e2e or CPU legs): the "
                          "command to run under ncu; numbers printed then are not bench values")
@@ -267,6 +270,12 @@ def run_cuda(args):
     walker0 = rank * WALKERS
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    if args.micro_only:
+        if rank == 0:
+            print(json.dumps({"eval_microbench": eval_microbench(L, ctx, dev, flush,
+                                                                 args.micro_repeats)}), flush=True)
+        ctx.close()
+        return 0
 
     def init_state():
         x = torch.as_tensor(x0.reshape(-1), dtype=torch.float64, device=dev).contiguous()

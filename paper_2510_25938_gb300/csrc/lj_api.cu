@@ -157,7 +157,7 @@ ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p) {
   h.m = p->m; h.max_iter = p->max_iter; h.max_ls = p->max_ls;
   h.gtol = p->gtol; h.c1 = p->c1; h.c2 = p->c2; h.alpha_max = p->alpha_max;
   h.switch_gtol = p->switch_gtol; h.deadline = p->deadline_cycles;
-  h.eps = p->eps; h.sigma = p->sigma;
+  h.k = ljh::make_consts(p->eps, p->sigma);
   return h;
 }
 
@@ -302,8 +302,7 @@ lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precisio
   a.x = d_x;
   a.energy = d_energy;
   a.grad = d_grad;
-  a.eps = eps;
-  a.sigma = sigma;
+  a.k = ljh::make_consts(eps, sigma);
   cudaError_t e = ljh::eval_launch(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lj_energy_grad_batched launch");
   return LJ_OK;

@@ -33,7 +33,7 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
   MinParams p;
   p.m = h.m; p.max_iter = h.max_iter; p.max_ls = h.max_ls;
   p.gtol = h.gtol; p.c1 = h.c1; p.c2 = h.c2; p.alpha_max = h.alpha_max;
-  p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.eps = h.eps; p.sigma = h.sigma;
+  p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.k = h.k;
   p.f32_resolution = h.f32_resolution; p.df_resolution = h.df_resolution;
   return p;
 }

@@ -237,47 +237,85 @@ template <typename X> struct PosOf;
 template <> struct PosOf<float> { using type = PosF; };
 template <> struct PosOf<double> { using type = PosD; };
 
-// FP32: 4-term blocks summed in FP32, folded into a float-float accumulator.
-__device__ __forceinline__ void pair_row_f32(int n, int i, float px, float py, float pz,
-                                             const PosF* __restrict__ pos, float sig2,
-                                             float& ax, float& ay, float& az, ff& e) {
-  ax = 0.f; ay = 0.f; az = 0.f;
-  int j = 0;
-  for (; j + 4 <= n; j += 4) {
-    float eb = 0.f;
+// ---------------------------------------------------------------------------
+// FP32 pair rows on packed float pairs (sm_100+ FADD2 / FMUL2 / FFMA2: two
+// IEEE single operations per instruction, each rounded exactly like its
+// scalar form).  Positions are staged two atoms per 32-byte record, atoms
+// 2m and 2m+1 in record m (unscaled: differences of the given coordinates
+// are the exact-as-possible inputs of r2, and sigma enters as one product
+// sigma^2 / r2 where sigma != 1); an odd cluster
+// pads its last record with kFarAtom, whose terms underflow to exactly zero
+// (r2 ~ 4e36 keeps 1/r2 normal, (1/r2)^2 rounds to 0), so every record holds
+// two live lanes and no lane needs a bounds test.  One instruction then
+// serves two pair terms, which halves the issue slots of the FP32 row: the
+// row is bound by the FMA pipe instead of by instruction issue.
+// ---------------------------------------------------------------------------
+struct alignas(16) PosF2 {
+  float x[2], y[2], z[2], w[2];
+};
+constexpr float kFarAtom = 0x1p60f;
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// stage atom i into its record; the owner of the last atom of an odd
+// cluster also writes the padding lane
+__device__ __forceinline__ void stage_f32x2(PosF2* pos, int n, int i, float x, float y, float z) {
+  PosF2& r = pos[i >> 1];
+  const int l = i & 1;
+  r.x[l] = x; r.y[l] = y; r.z[l] = z;
+  if (i == n - 1 && l == 0) {
+    r.x[1] = kFarAtom; r.y[1] = kFarAtom; r.z[1] = kFarAtom;
+  }
+}
+
+// One-sided row of atom i (position px, py, pz) against the n atoms of
+// `pos`: b = sum_j c_ij (x_j - x_i) with c = s2 s6 (2 s6 - 1), s2 = sigma^2
+// / r^2 (SIG: sigma != 1, sig2 = sigma^2), and e += sum_j s6 (s6 - 1), the
+// self term excluded.  Energy: per lane, blocks of 4 terms summed in FP32,
+// the two lanes' block sums added and folded into the float-float `e`.
+template <bool SIG>
+__device__ __forceinline__ void pair_row_f32x2(int n, int i, float px, float py, float pz,
+                                               const PosF2* __restrict__ pos, float sig2,
+                                               float& bx, float& by, float& bz, ff& e) {
+  const int M = (n + 1) >> 1;
+  const float2 npx = f2(-px), npy = f2(-py), npz = f2(-pz), m1 = f2(-1.f);
+  const int sx = (i & 1) ? -1 : (i >> 1);     // record whose lane 0 is atom i
+  const int sy = (i & 1) ? (i >> 1) : -1;     // record whose lane 1 is atom i
+  float2 ax = f2(0.f), ay = f2(0.f), az = f2(0.f);
+  auto term = [&](int m, float2& eb) {
+    const float4 xy = *reinterpret_cast<const float4*>(&pos[m].x[0]);
+    const float2 zz = *reinterpret_cast<const float2*>(&pos[m].z[0]);
+    const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
+    const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
+    const float2 dz = __fadd2_rn(zz, npz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float2 s2;
+    s2.x = (m == sx) ? 0.f : rcp_approx(r2.x);
+    s2.y = (m == sy) ? 0.f : rcp_approx(r2.y);
+    if constexpr (SIG) s2 = __fmul2_rn(s2, f2(sig2));
+    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+    const float2 t = __fadd2_rn(s6, m1);
+    eb = __ffma2_rn(s6, t, eb);
+    const float2 c = __fmul2_rn(__fmul2_rn(s2, s6), __fadd2_rn(s6, t));
+    ax = __ffma2_rn(c, dx, ax);
+    ay = __ffma2_rn(c, dy, ay);
+    az = __ffma2_rn(c, dz, az);
+  };
+  int m = 0;
+  for (; m + 4 <= M; m += 4) {
+    float2 eb = f2(0.f);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const PosF q = pos[j + u];
-      const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float ir2 = (j + u == i) ? 0.f : rcp_approx(r2);
-      const float s2 = sig2 * ir2;
-      const float s6 = s2 * s2 * s2;
-      const float t = s6 - 1.f;
-      eb = fmaf(s6, t, eb);
-      const float c = (s2 * s6) * (s6 + t);
-      ax = fmaf(c, dx, ax);
-      ay = fmaf(c, dy, ay);
-      az = fmaf(c, dz, az);
-    }
-    e = ff_add_f(e, eb);
+    for (int u = 0; u < 4; ++u) term(m + u, eb);
+    e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
   }
-  float eb = 0.f;
-  for (; j < n; ++j) {
-    const PosF q = pos[j];
-    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir2 = (j == i) ? 0.f : rcp_approx(r2);
-    const float s2 = sig2 * ir2;
-    const float s6 = s2 * s2 * s2;
-    const float t = s6 - 1.f;
-    eb = fmaf(s6, t, eb);
-    const float c = (s2 * s6) * (s6 + t);
-    ax = fmaf(c, dx, ax);
-    ay = fmaf(c, dy, ay);
-    az = fmaf(c, dz, az);
+  if (m < M) {
+    float2 eb = f2(0.f);
+    for (; m < M; ++m) term(m, eb);
+    e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
   }
-  e = ff_add_f(e, eb);
+  bx = __fadd_rn(ax.x, ax.y);
+  by = __fadd_rn(ay.x, ay.y);
+  bz = __fadd_rn(az.x, az.y);
 }
 
 // Double-double helpers: exact sum a + b = s + e (Knuth TwoSum).

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/lj_bh.h"
+#include "lj_consts.h"
 
 namespace ljd { struct MinParams; }
 
@@ -14,7 +15,7 @@ struct MinParamsH {     // mirror of ljd::MinParams (plain data)
   int m, max_iter, max_ls;
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
-  double eps, sigma;
+  LjConsts k;             // Eq. (1) constants from eps and sigma
   double f32_resolution, df_resolution;   // handover thresholds, relative to |E|
 };
 
@@ -28,7 +29,7 @@ struct EvalArgs {
   const void* x;
   double* energy;
   void* grad;
-  double eps, sigma;
+  LjConsts k;           // Eq. (1) constants from eps and sigma
 };
 
 struct LbfgsArgs {

@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "lj_device.cuh"
+#include "lj_consts.h"
 #include "../../include/lj_bh.h"
 
 namespace ljd {
@@ -43,7 +44,7 @@ struct MinParams {
   int m, max_iter, max_ls;
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
-  double eps, sigma;
+  ljh::LjConsts k;         // Eq. (1) constants from eps and sigma (host-derived)
   double f32_resolution;   // FP32 phase hands over below this predicted decrease / |E|
   double df_resolution;    // double-float polish hands over below this / |E|
 };
@@ -131,9 +132,6 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   using V = typename P::V;
   using S = typename P::S;
   constexpr int PM = P::PM;
-  using XR = std::conditional_t<std::is_same<X, float>::value, float, double>;   // pair-term real
-  const XR sig2 = (XR)(p.sigma * p.sigma);
-  const XR gscale = (XR)(24.0 * p.eps / (p.sigma * p.sigma));
   tm.sync();  // previous readers of pos are done
 #pragma unroll
   for (int a = 0; a < A; ++a) {
@@ -142,11 +140,13 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
       if constexpr (PM == 1) {
         // double-float positions, scaled by 1/sigma (exact for sigma = 1)
         ff qx = x[a][0], qy = x[a][1], qz = x[a][2];
-        if (p.sigma != 1.0) {
-          const ff is = df_from_double(1.0 / p.sigma);
+        if (p.k.sigma != 1.0) {
+          const ff is{p.k.is_hi, p.k.is_lo};
           qx = df_mul(qx, is); qy = df_mul(qy, is); qz = df_mul(qz, is);
         }
         static_cast<PosDF*>(posv)[i] = PosDF{qx.hi, qy.hi, qz.hi, 0.f, qx.lo, qy.lo, qz.lo, 0.f};
+      } else if constexpr (sizeof(X) == 4) {
+        stage_f32x2(static_cast<PosF2*>(posv), n, i, x[a][0], x[a][1], x[a][2]);   // packed
       } else {
         typename PosOf<X>::type q;
         q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
@@ -190,7 +190,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           pair_advance(n, 2 * T, i2, j2);
         }
         tm.sync();
-        const float gs = (float)(24.0 * p.eps / p.sigma);
+        const float gs = p.k.gs_f;
         for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
           const int ii = q3 / 3;
           const ff* vc = vb + (q3 - 3 * ii) * np;
@@ -212,11 +212,11 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
         tm.sync();
         // float-float team sum (FP32 pipes): its ~2^-47 relative error is far
         // below the double-float handover resolution
-        E = ff_scale(team_sum_ff<T>(tm, e), (float)(4.0 * p.eps));
+        E = ff_scale(team_sum_ff<T>(tm, e), p.k.e4_f);
       } else {
         const PosD* pos = static_cast<const PosD*>(posv);
         double* vb = static_cast<double*>(hbuf);
-        const double sig2 = p.sigma * p.sigma;
+        const double sig2 = p.k.sig2;
         dd e{0.0, 0.0};
         for (int q = tm.rank; q < np; q += 2 * T) {
           const bool two = q + T < np;
@@ -237,7 +237,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           pair_advance(n, 2 * T, i2, j2);
         }
         tm.sync();
-        const double gs = 24.0 * p.eps / sig2;
+        const double gs = p.k.gscale;
         for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
           const int ii = q3 / 3;
           const double* vc = vb + (q3 - 3 * ii) * np;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           gsum[q3] = -gs * (s0 + s1);
         }
         tm.sync();
-        E = team_sum_dd<T>(tm, e) * (4.0 * p.eps);
+        E = team_sum_dd<T>(tm, e) * p.k.e4;
       }
 #pragma unroll
       for (int a = 0; a < A; ++a) {
@@ -272,7 +272,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   }
   if constexpr (PM == 1) {
     const PosDF* pos = static_cast<const PosDF*>(posv);
-    const float gs = (float)(24.0 * p.eps / p.sigma);
+    const float gs = p.k.gs_f;
     ff e{0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
@@ -290,18 +290,23 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
       }
       if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
     }
-    E = ff_scale(team_sum_ff<T>(tm, e), (float)(2.0 * p.eps));
+    E = ff_scale(team_sum_ff<T>(tm, e), p.k.e2_f);
   } else if constexpr (sizeof(X) == 4) {
-    const PosF* pos = static_cast<const PosF*>(posv);
+    const PosF2* pos = static_cast<const PosF2*>(posv);
+    const float gs = p.k.gscale_f;
+    const bool unit = p.k.sigma == 1.0;
     ff e{0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int i = tm.rank + a * T;
       if (i < n) {
-        float ax, ay, az;
+        float bx, by, bz;
         ff ea{0.f, 0.f};
-        pair_row_f32(n, i, x[a][0], x[a][1], x[a][2], pos, sig2, ax, ay, az, ea);
-        g[a][0] = -gscale * ax; g[a][1] = -gscale * ay; g[a][2] = -gscale * az;
+        if (unit)
+          pair_row_f32x2<false>(n, i, x[a][0], x[a][1], x[a][2], pos, 1.f, bx, by, bz, ea);
+        else
+          pair_row_f32x2<true>(n, i, x[a][0], x[a][1], x[a][2], pos, p.k.sig2_f, bx, by, bz, ea);
+        g[a][0] = gs * bx; g[a][1] = gs * by; g[a][2] = gs * bz;
         e = ff_add(e, ea);
       } else {
         g[a][0] = 0.f; g[a][1] = 0.f; g[a][2] = 0.f;
@@ -309,7 +314,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
       if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
     }
     ff et = team_sum_ff<T>(tm, e);
-    E = ff_scale(et, (float)(2.0 * p.eps));
+    E = ff_scale(et, p.k.e2_f);
   } else {
     const PosD* pos = static_cast<const PosD*>(posv);
     dd e{0.0, 0.0};
@@ -318,14 +323,14 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
       const int i = tm.rank + a * T;
       if (i < n) {
         double ax, ay, az;
-        pair_row_f64(n, i, x[a][0], x[a][1], x[a][2], pos, sig2, ax, ay, az, e);
-        g[a][0] = -gscale * ax; g[a][1] = -gscale * ay; g[a][2] = -gscale * az;
+        pair_row_f64(n, i, x[a][0], x[a][1], x[a][2], pos, p.k.sig2, ax, ay, az, e);
+        g[a][0] = -p.k.gscale * ax; g[a][1] = -p.k.gscale * ay; g[a][2] = -p.k.gscale * az;
       } else {
         g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
       }
       if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
     }
-    E = team_sum_dd<T>(tm, e) * (2.0 * p.eps);
+    E = team_sum_dd<T>(tm, e) * p.k.e2;
   }
   if (d) dphi = (S)team_sum1<T, V>(tm, dp);
 }

@@ -45,3 +45,21 @@ def numpy_energy_grad(x, eps=1.0, sigma=1.0):
 def grad_scale(x, eps=1.0, sigma=1.0):
     p, n, d, s6, c = _pair_terms(x, eps, sigma)
     return float(np.linalg.norm((np.abs(c)[:, :, None] * np.abs(d)).sum(1)))
+
+
+def energy_scale(x, eps=1.0, sigma=1.0):
+    """No-cancellation scale of Eq. (1): 4 eps sum_{i<j} (s12 + s6), the bound
+    that a sum of rounded pair terms has its error measured against."""
+    p, n, d, s6, c = _pair_terms(x, eps, sigma)
+    return float(2.0 * eps * (s6 * s6 + s6).sum())
+
+
+def grad_scale_terms(x, eps=1.0, sigma=1.0):
+    """Term-wise no-cancellation scale of the gradient: the norm of
+    sum_j 24 eps (2 s12 + s6) / r^2 |x_i - x_j|, which stays away from zero
+    where a pair sits at the minimum of its term (2 s12 = s6)."""
+    p, n, d, s6, c = _pair_terms(x, eps, sigma)
+    r2 = (d ** 2).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    cn = 24.0 * eps * (2 * s6 * s6 + s6) / r2
+    return float(np.linalg.norm((cn[:, :, None] * np.abs(d)).sum(1)))

@@ -15,13 +15,19 @@ import pytest
 
 import oracle as O
 from paper_2510_25938_gb300 import inputs as I
-from tests.helpers import fingerprint, grad_scale, numpy_energy_grad, same_basin
+from tests.helpers import (energy_scale, fingerprint, grad_scale, grad_scale_terms,
+                           numpy_energy_grad, same_basin)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_REL_E = 1e-10
 MIX_REL_E = 1e-6
+# FP32 pair terms on arbitrary (overlapping) geometries, against the
+# no-cancellation scales: r2 carries <= ~4 u (u = 2^-24) and 1/r2 another
+# 2 u (rcp.approx), which the 6th and 12th powers multiply, plus a few
+# roundings: <= ~50 u per term; 64 u bounds it.
+FP32_NC_REL = 64 * 2.0 ** -24
 MIX_ABS_FINAL = 1e-6
 GTOL = 1e-6
 
@@ -140,6 +146,64 @@ def test_eval_jittered_minima_uniform_batch(lj, ctx, prec, xdt, rel):
     for c in range(n_cand):
         scale = max(np.linalg.norm(g_ref[c]), grad_scale(xin[c]))
         assert np.linalg.norm(g[c] - g_ref[c]) <= rel * scale
+
+
+# (N, candidates): padded odd N, several tiles per CTA (the flat layout runs
+# 2 CTAs per SM over tiles of floor(512 / N) candidates), and the extremes of
+# the flat layout (N = 2: 256 candidates per tile; N = 511, 512: one)
+FLAT_CASES = [(2, 3000), (13, 12500), (37, 6000), (38, 4100), (150, 900), (511, 30), (512, 20)]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("n_atoms,n_cand", FLAT_CASES)
+def test_eval_flat_uniform_sizes(lj, ctx, n_atoms, n_cand, prec):
+    """Uniform batches on the flat thread-per-atom layout against the oracle:
+    every energy and gradient, FP32 (prec 1, FP32 input) and FP64.  Errors
+    are measured against the no-cancellation scales (a random dimer near
+    r = sigma has E ~ 0 while its terms are ~4 eps).  Random cube starts hold
+    near-overlapping pairs, where FP32 terms reach tens of ulps (FP32_NC_REL);
+    the 1e-6 mixed-precision bound is checked on the evaluation workload
+    itself (jittered minima) above."""
+    x = I.cube_starts(n_cand, n_atoms, (n_atoms / 0.3) ** (1 / 3), I.workload_seed(3) + n_atoms)
+    xdt = torch.float32 if prec == 1 else torch.float64
+    xin = x.astype(np.float32).astype(np.float64) if prec == 1 else x
+    rel = FP32_NC_REL if prec == 1 else FP64_REL_E
+    e_ref, g_ref = O.eval_batch(xin, n_cand, uniform_n=n_atoms)
+    xd = _cuda(xin, xdt)
+    e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(xd)
+    lj.lj_energy_grad_batched(ctx, xd, e, g, n_cand=n_cand, uniform_n=n_atoms, prec=prec)
+    e = e.cpu().numpy()
+    g = g.cpu().numpy().reshape(n_cand, -1).astype(np.float64)
+    xr = xin.reshape(n_cand, -1)
+    escale = np.array([energy_scale(xr[c]) for c in range(n_cand)])
+    assert (np.abs(e - e_ref) <= rel * escale).all()
+    g_ref = g_ref.reshape(n_cand, -1)
+    err = np.linalg.norm(g - g_ref, axis=1)
+    scale = np.array([grad_scale_terms(xr[c]) for c in range(n_cand)])
+    assert (err <= rel * scale).all()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_eval_flat_eps_sigma(lj, ctx, prec):
+    """eps and sigma on the flat layout (FP32 divides coordinates by sigma)."""
+    n_cand, n_atoms = 700, 37
+    x = 1.3 * I.cube_starts(n_cand, n_atoms, (n_atoms / 0.3) ** (1 / 3), I.workload_seed(3) + 99)
+    xin = x.astype(np.float32).astype(np.float64) if prec == 1 else x
+    rel = FP32_NC_REL if prec == 1 else FP64_REL_E
+    e_ref, g_ref = O.eval_batch(xin, n_cand, uniform_n=n_atoms, eps=1.7, sigma=1.3)
+    xd = _cuda(xin, torch.float32 if prec == 1 else torch.float64)
+    e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(xd)
+    lj.lj_energy_grad_batched(ctx, xd, e, g, n_cand=n_cand, uniform_n=n_atoms, prec=prec,
+                              eps=1.7, sigma=1.3)
+    e = e.cpu().numpy()
+    g = g.cpu().numpy().reshape(n_cand, -1).astype(np.float64)
+    xr = xin.reshape(n_cand, -1)
+    for c in range(n_cand):
+        assert abs(e[c] - e_ref[c]) <= rel * energy_scale(xr[c], 1.7, 1.3)
+        scale = grad_scale_terms(xr[c], 1.7, 1.3)
+        assert np.linalg.norm(g[c] - g_ref.reshape(n_cand, -1)[c]) <= rel * scale
 
 
 def test_eval_degenerate_inputs(lj, ctx):
