@@ -421,7 +421,8 @@ def run_cuda(args):
                       "achieved_tflops": flops_64path / t64 / 1e12,
                       "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS},
         "work": {k: st_mix[k] for k in ("evals32", "evals64", "evals_df", "iters32", "iters64",
-                                        "cycles32", "cycles_df", "cycles64")},
+                                        "cycles32", "cycles_df", "cycles64", "cycles_direction",
+                                        "cycles_linesearch")},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,

@@ -393,9 +393,10 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 //   f32_resolution |E| (default 4 FP32 ulps), or when a line search fails;
 //   never converges.
 // MODE 2 (mixed, double-float polish): CONVERGED on ||g||_inf < gtol (to be
-//   confirmed in FP64); hands over to FP64 once the predicted decrease is
-//   below df_resolution |E| (default 32 * 2^-48), or when a line search
-//   fails.
+//   confirmed in FP64); once the predicted decrease is below df_resolution
+//   |E| (default 32 * 2^-48) its line searches accept steps on the gradient
+//   alone (approximate Wolfe conditions); hands over to FP64 when a line
+//   search fails.
 // ---------------------------------------------------------------------------
 template <int T, int A, typename P, int MODE>
 __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
@@ -416,6 +417,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
   const XG stop_gtol = MODE == 1 ? (XG)p.switch_gtol : (XG)p.gtol;
   V alpha[LJ_MAX_M];
   V d[A][3];
+  bool gmode = false;   // MODE 2: energy below resolution, gradient-only line search
   X xt[A][3];
   XG gt[A][3];
   while (iters < p.max_iter) {
@@ -555,9 +557,13 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         a1 = (S)1 / S_sqrt(-dphi0);
         if (a1 > (S)1) a1 = (S)1;
       }
-      if constexpr (MODE == 1 || MODE == 2) {
+      if constexpr (MODE == 1) {
         // predicted decrease below this tier's energy resolution: hand over
         if (-dphi0 * a1 < resolution * fabsf(f.hi)) return PH_SWITCH;
+      } else if constexpr (MODE == 2) {
+        // below the double-float energy resolution: from here on, steps are
+        // accepted on the gradient (accurate to ~1e-11 here) instead
+        if (-dphi0 * a1 < resolution * fabsf(f.hi)) gmode = true;
       }
       // ---- strong-Wolfe line search ----------------------------------------
       int ev = 0;
@@ -580,6 +586,45 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         ++ev;
         last_a = al;
       };
+      bool gsearch = false;
+      if constexpr (MODE == 2) {
+      if (gmode) {
+        gsearch = true;
+        // ---- gradient-only search (approximate Wolfe conditions, Hager and
+        // Zhang 2005): accept |phi'(a)| <= c2 |phi'(0)| with the energy no
+        // more than the resolution above f(0) (which, for a near-quadratic
+        // phi, also implies the Armijo decrease); bracket on the sign of
+        // phi' and interpolate by secant steps on phi'.
+        const S tol_f = (S)2 * resolution * fabsf(f.hi);
+        S glo = (S)0, ghi = (S)-1, dlo = dphi0, dhi = (S)0;
+        bool hi_slope = false;
+        while (ev < p.max_ls) {
+          F fa;
+          trial(a, fa, dp);
+          const bool eok = fisfinite(fa) && isfinite(dp) && (S)fdiff(fa, f) <= tol_f;
+          if (!eok || dp > -c2 * dphi0) {          // too long
+            ghi = a; dhi = dp; hi_slope = eok;
+          } else if (dp < c2 * dphi0) {            // too short
+            glo = a; dlo = dp;
+          } else {
+            ft = fa; done = true;
+            break;
+          }
+          if (ghi < (S)0) {
+            a = (S)2 * a;
+            if (a > amax) a = amax;
+          } else {
+            const S w = ghi - glo;
+            S t = (hi_slope && dhi > dlo) ? glo - dlo * w / (dhi - dlo) : glo + (S)0.5 * w;
+            const S tlo = glo + (S)0.1 * w, thi = ghi - (S)0.1 * w;
+            if (!(t >= tlo)) t = tlo;
+            if (!(t <= thi)) t = thi;
+            a = t;
+          }
+        }
+      }
+      }
+      if (!gsearch) {
       for (int i = 1; !done && !zoom; ++i) {
         if (ev >= p.max_ls) break;
         F fa;
@@ -635,6 +680,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
           ft = best_f;
         }
         done = true;
+      }
       }
       evals += ev;
       ok = done;
