@@ -383,15 +383,126 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 }
 
 // ---------------------------------------------------------------------------
+// Two-loop recursion by the team's first warp (float history, teams of 2 to 4
+// warps).  The recursion is a chain of 2 cnt + 1 dependent inner products;
+// done by the whole team, each one crosses warps through shared memory and a
+// barrier.  Instead every thread stages its gradient in `xb` (the idle
+// position buffer, 12 A T + 4 bytes), warp 0 runs the recursion over all T
+// ranks' entries (lane l covers ranks l, l + 32, ...: the history is
+// addressable by rank) with shuffle-only reductions, and stages d and
+// g.d back: two team barriers per direction instead of 2 cnt + 1.  Same
+// operations and order as the team version, per warp-sized partial sums.
+// ---------------------------------------------------------------------------
+template <int V0>
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int T, int A, typename XG>
+__device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt, int head,
+                                               const float* __restrict__ Sh,
+                                               const float* __restrict__ Yh,
+                                               const float (&rho)[LJ_MAX_M],
+                                               const float (&gmv)[LJ_MAX_M],
+                                               const XG (&g)[A][3], float* xb,
+                                               float (&d)[A][3]) {
+  constexpr int W = T / 32;
+#pragma unroll
+  for (int a = 0; a < A; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xb[(a * 3 + c) * T + tm.rank] = (float)g[a][c];
+  tm.sync();
+  if (tm.rank < 32) {
+    const int lane = tm.rank;
+    auto slot_of = [&](int t) { const int sl = head + t; return sl >= m ? sl - m : sl; };
+    float q[W][A][3], gl[W][A][3];
+    float alpha[LJ_MAX_M];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gl[w][a][c] = xb[(a * 3 + c) * T + lane + 32 * w];
+          q[w][a][c] = gl[w][a][c];
+        }
+    for (int t = cnt - 1; t >= 0; --t) {
+      const int sl = slot_of(t);
+      float part = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            part += Sh[hidx<T, A>(sl, a, c, lane + 32 * w)] * q[w][a][c];
+      const float al = rho[sl] * warp_sum<0>(part);
+      alpha[t] = al;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q[w][a][c] -= al * Yh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+    }
+    const float gam = gmv[slot_of(cnt - 1)];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[w][a][c] *= gam;
+    for (int t = 0; t < cnt; ++t) {
+      const int sl = slot_of(t);
+      float part = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            part += Yh[hidx<T, A>(sl, a, c, lane + 32 * w)] * q[w][a][c];
+      const float coef = alpha[t] - rho[sl] * warp_sum<0>(part);
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q[w][a][c] += coef * Sh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+    }
+    float part = 0.f;
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+      for (int a = 0; a < A; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          xb[(a * 3 + c) * T + lane + 32 * w] = -q[w][a][c];
+          part += gl[w][a][c] * -q[w][a][c];
+        }
+    const float dphi = warp_sum<0>(part);
+    if (lane == 0) xb[A * 3 * T] = dphi;
+  }
+  tm.sync();
+#pragma unroll
+  for (int a = 0; a < A; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d[a][c] = xb[(a * 3 + c) * T + tm.rank];
+  return xb[A * 3 * T];
+}
+
+// ---------------------------------------------------------------------------
 // One L-BFGS phase: iterate from (x, g, f) until a stop condition.
 // X: coordinates/gradient precision, V: direction/history precision,
 // PM: pair arithmetic (0 native X, 1 double-float).
 // MODE 0 (FP64, final): stops on ||g||_inf < gtol (CONVERGED) or a failed
 //   line search (LSFAIL).
 // MODE 1 (mixed, FP32 phase): hands over (SWITCH) once ||g||_inf <
-//   switch_gtol, once the predicted decrease -alpha phi'(0) is below
-//   f32_resolution |E| (default 4 FP32 ulps), or when a line search fails;
-//   never converges.
+//   switch_gtol or when a line search fails; never converges.  Once the
+//   predicted decrease -alpha phi'(0) is below f32_resolution |E| (default 4
+//   FP32 ulps) its line searches accept steps on the gradient alone.
 // MODE 2 (mixed, double-float polish): CONVERGED on ||g||_inf < gtol (to be
 //   confirmed in FP64); once the predicted decrease is below df_resolution
 //   |E| (default 32 * 2^-48) its line searches accept steps on the gradient
@@ -402,7 +513,7 @@ template <int T, int A, typename P, int MODE>
 __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
                          typename P::XG (&g)[A][3], typename P::F& f,
                          typename P::V* __restrict__ Sh, typename P::V* __restrict__ Yh,
-                         typename P::V (&sy)[LJ_MAX_M], typename P::V (&yy)[LJ_MAX_M], int& cnt,
+                         typename P::V (&rho)[LJ_MAX_M], typename P::V (&gmv)[LJ_MAX_M], int& cnt,
                          int& head, int& iters,
                          int& evals, int& phase_iters, long long& vec, void* pos,
                          void* hbuf, const MinParams& p, long long t0, long long (&cyc)[2]) {
@@ -417,14 +528,23 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
   const XG stop_gtol = MODE == 1 ? (XG)p.switch_gtol : (XG)p.gtol;
   V alpha[LJ_MAX_M];
   V d[A][3];
-  bool gmode = false;   // MODE 2: energy below resolution, gradient-only line search
+  bool gmode = false;   // MODE 1, 2: energy below resolution, gradient-only line search
   X xt[A][3];
   XG gt[A][3];
   while (iters < p.max_iter) {
     // ---- search direction -------------------------------------------------
     long long tc = clock64();
     S dphi0 = (S)1;
-    if (cnt > 0) {
+    bool led = false;
+    if constexpr (std::is_same<V, float>::value && T > 32 && T <= 128) {
+      if (cnt > 0 && 12 * A * T + 4 <= 32 * n) {
+        dphi0 = (S)lead_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh, rho, gmv, g,
+                                           static_cast<float*>(pos), d);
+        vec += (long long)cnt * 3 * n;
+        led = true;
+      }
+    }
+    if (cnt > 0 && !led) {
       V q[A][3];
 #pragma unroll
       for (int a = 0; a < A; ++a)
@@ -444,7 +564,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
             yc[a][c] = Yh[hidx<T, A>(sl, a, c, tm.rank)];
           }
       }
-      V rho_c = (V)1 / sy[slot_of(cnt - 1)];
+      V rho_c = rho[slot_of(cnt - 1)];
       for (int t = cnt - 1; t >= 0; --t) {
         const int nsl = slot_of(t > 0 ? t - 1 : 0);
 #pragma unroll
@@ -454,7 +574,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
             sn[a][c] = Sh[hidx<T, A>(nsl, a, c, tm.rank)];
             yn[a][c] = Yh[hidx<T, A>(nsl, a, c, tm.rank)];
           }
-        const V rho_n = (V)1 / sy[nsl];
+        const V rho_n = rho[nsl];
         V part = (V)0;
 #pragma unroll
         for (int a = 0; a < A; ++a)
@@ -473,13 +593,13 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         rho_c = rho_n;
       }
       const int newest = slot_of(cnt - 1);
-      const V gam = sy[newest] / yy[newest];
+      const V gam = gmv[newest];
 #pragma unroll
       for (int a = 0; a < A; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) q[a][c] *= gam;
       // (sc, yc) now hold the oldest pair, the first one of the second loop
-      rho_c = (V)1 / sy[slot_of(0)];
+      rho_c = rho[slot_of(0)];
       for (int t = 0; t < cnt; ++t) {
         const int nsl = slot_of(t + 1 < cnt ? t + 1 : t);
 #pragma unroll
@@ -489,7 +609,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
             sn[a][c] = Sh[hidx<T, A>(nsl, a, c, tm.rank)];
             yn[a][c] = Yh[hidx<T, A>(nsl, a, c, tm.rank)];
           }
-        const V rho_n = (V)1 / sy[nsl];
+        const V rho_n = rho[nsl];
         V part = (V)0;
 #pragma unroll
         for (int a = 0; a < A; ++a)
@@ -557,12 +677,10 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         a1 = (S)1 / S_sqrt(-dphi0);
         if (a1 > (S)1) a1 = (S)1;
       }
-      if constexpr (MODE == 1) {
-        // predicted decrease below this tier's energy resolution: hand over
-        if (-dphi0 * a1 < resolution * fabsf(f.hi)) return PH_SWITCH;
-      } else if constexpr (MODE == 2) {
-        // below the double-float energy resolution: from here on, steps are
-        // accepted on the gradient (accurate to ~1e-11 here) instead
+      if constexpr (MODE == 1 || MODE == 2) {
+        // predicted decrease below this tier's energy resolution: from here
+        // on, steps are accepted on the gradient instead (the FP32 gradient
+        // is trusted down to switch_gtol, the double-float one to ~1e-11)
         if (-dphi0 * a1 < resolution * fabsf(f.hi)) gmode = true;
       }
       // ---- strong-Wolfe line search ----------------------------------------
@@ -587,7 +705,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         last_a = al;
       };
       bool gsearch = false;
-      if constexpr (MODE == 2) {
+      if constexpr (MODE == 1 || MODE == 2) {
       if (gmode) {
         gsearch = true;
         // ---- gradient-only search (approximate Wolfe conditions, Hager and
@@ -718,8 +836,8 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
           Sh[hidx<T, A>(slot, a, c, tm.rank)] = sv[a][c];
           Yh[hidx<T, A>(slot, a, c, tm.rank)] = yv[a][c];
         }
-      sy[slot] = pr[0];
-      yy[slot] = pr[1];
+      rho[slot] = (V)1 / pr[0];      // rho = 1 / s.y and the scaling s.y / y.y, formed
+      gmv[slot] = pr[0] / pr[1];     // once here instead of in every recursion step
     }
 #pragma unroll
     for (int a = 0; a < A; ++a)
@@ -792,9 +910,9 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       r.E = f; r.status = ST_NONFINITE; lap(r.cyc64); return;
     }
     if (gm < p.gtol) { r.E = f; lap(r.cyc64); return; }
-    double sy[LJ_MAX_M], yy[LJ_MAX_M];
+    double rho[LJ_MAX_M], gmv[LJ_MAX_M];
     double* Sh = (double*)hist;
-    const int code = run_phase<T, A, PrecF64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, sy, yy, cnt,
+    const int code = run_phase<T, A, PrecF64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, rho, gmv, cnt,
                                                  head, iters, r.evals64, r.iters64, r.vec64, pos,
                                                  hbuf, p, t0, cyc);
     r.E = f;
@@ -804,7 +922,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
   } else {
     float* Sh = (float*)hist;
     float* Yh = Sh + hstride;
-    float sy[LJ_MAX_M], yy[LJ_MAX_M];
+    float rho[LJ_MAX_M], gmv[LJ_MAX_M];
     int code = PH_SWITCH;
     float dummy32;
     // ---- tier 1: FP32 -------------------------------------------------------
@@ -821,7 +939,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       r.evals32 = 1;
       const float gm = grad_max<T, A, float>(tm, g32);
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
-        code = run_phase<T, A, PrecF32, 1>(tm, n, x32, g32, f32, Sh, Yh, sy, yy, cnt, head,
+        code = run_phase<T, A, PrecF32, 1>(tm, n, x32, g32, f32, Sh, Yh, rho, gmv, cnt, head,
                                            iters, r.evals32, r.iters32, r.vec32, pos, nullptr, p,
                                            t0, cyc);
         moved32 = r.iters32 > 0;
@@ -857,7 +975,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
           need_fp64 = true;               // confirm (and finish) in FP64
           break;
         }
-        code = run_phase<T, A, PrecDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, sy, yy, cnt, head, iters,
+        code = run_phase<T, A, PrecDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, rho, gmv, cnt, head, iters,
                                           r.evals_df, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
         if (code == PH_CONVERGED) {
           gm = 0.f;
@@ -886,7 +1004,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       if (gm < p.gtol) {
         r.E = f; r.iters = iters; r.status = ST_CONVERGED; lap(r.cyc64); return;
       }
-      code = run_phase<T, A, PrecF64m, 0>(tm, n, x64, g, f, Sh, Yh, sy, yy, cnt, head, iters,
+      code = run_phase<T, A, PrecF64m, 0>(tm, n, x64, g, f, Sh, Yh, rho, gmv, cnt, head, iters,
                                           r.evals64, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
       r.E = f;
       r.iters = iters;
