@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true", help="skip the evaluation microbench")
+    ap.add_argument("--workload", default="lj38-bh",
+                    choices=["lj38-bh", "uneven-4096", "large-500", "large-1000", "lj13-seq"],
+                    help="lj38-bh (default): the Basin Hopping step this bench reports; the "
+                         "others time the batched minimisation of the uneven and large-cluster "
+                         "workloads, or one sequential FP64 LJ13 walker, and print their own line")
     ap.add_argument("--micro-only", action="store_true",
                     help="run only the evaluation microbench and print its JSON")
     ap.add_argument("--micro-repeats", type=int, default=100)
@@ -430,7 +435,7 @@ def run_cuda(args):
     if achieved_tf is not None:
         line["roofline"] = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                            "traffic": None, "kernel": "bh_cluster_kernel<32,2,mixed>",
+                            "traffic": None, "kernel": "bh_cluster_kernel<64,1,mixed>",
                             "fp64_flop_share": flops64 / flops if flops else None}
     if e2e:
         line["e2e"] = e2e
@@ -446,10 +451,141 @@ def run_cuda(args):
     return 0
 
 
+# other workloads (one GPU): (name, n_cand, N range, start kind, m)
+BATCH_WORKLOADS = {
+    "uneven-4096": dict(n_cand=4096, n_lo=13, n_hi=150, kind="cube", m=10, cfg=3,
+                        desc="4,096 candidates, N uniform in [13, 150], cube starts at "
+                             "reduced density 0.3, bucketed persistent launches, m=10"),
+    "large-500": dict(n_cand=1024, n_lo=500, n_hi=500, kind="fcc", m=20, cfg=4,
+                      desc="1,024 candidates of N=500, fcc fragments jittered 0.1 sigma, m=20"),
+    "large-1000": dict(n_cand=256, n_lo=1000, n_hi=1000, kind="fcc", m=20, cfg=4,
+                       desc="256 candidates of N=1000, fcc fragments jittered 0.1 sigma, m=20"),
+}
+
+
+def run_batch_workload(args):
+    """Batched minimisation of one workload, mixed and FP64, each timed with
+    CUDA events around lbfgs_minimize_batched (inputs resident, L2 flushed
+    before each timed call); converged minimisations per second."""
+    import torch
+    from paper_2510_25938_gb300 import build as B
+    B.build()
+    from paper_2510_25938_gb300 import inputs as I
+    from paper_2510_25938_gb300 import lj_bh as L
+    w = BATCH_WORKLOADS[args.workload]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    seed = I.workload_seed(w["cfg"])
+    if w["kind"] == "cube":
+        sizes = I.uneven_sizes(w["n_cand"], w["n_lo"], w["n_hi"], seed)
+        x0, off = I.uneven_cube_starts(sizes, 0.3, seed + 1)
+        uniform = 0
+    else:
+        x0 = I.fcc_fragments(w["n_cand"], w["n_lo"], 0.1, seed + w["n_lo"]).reshape(-1)
+        off = None
+        uniform = w["n_lo"]
+    n_cand = w["n_cand"]
+    ctx = L.Ctx(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    offd = torch.as_tensor(off, device=dev) if off is not None else None
+    out = {}
+    for prec, name in ((L.LJ_PREC_MIXED, "mixed"), (L.LJ_PREC_FP64, "fp64")):
+        times, conv = [], 0
+        for rep in range(max(args.warmup, 1) + args.steps):
+            x = torch.as_tensor(x0, dtype=torch.float64, device=dev).contiguous()
+            e = torch.empty(n_cand, dtype=torch.float64, device=dev)
+            st = torch.empty(n_cand, dtype=torch.int32, device=dev)
+            stats = L.new_stats(dev)
+            flush.fill_(float(rep))
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            kw = dict(atom_offset=offd, max_n=w["n_hi"]) if offd is not None else dict(
+                uniform_n=uniform)
+            ev0.record()
+            L.lbfgs_minimize_batched(ctx, x, e, st, None, None, stats, n_cand=n_cand,
+                                     params=L.LbfgsParams(prec=prec, m=w["m"]), **kw)
+            ev1.record()
+            torch.cuda.synchronize()
+            if rep >= max(args.warmup, 1):
+                times.append(ev0.elapsed_time(ev1) / 1e3)
+                conv = L.stats_dict(stats)["converged"]
+        t = sum(times) / len(times)
+        out[name] = {"value": conv / t, "ms_per_batch": 1e3 * t, "converged_fraction": conv / n_cand}
+    line = {"metric": "converged LJ minimisations/s", "value": out["mixed"]["value"],
+            "unit": "converged minimisations/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": w["desc"], "precision": "mixed",
+                                            "l2": "flushed (256 MiB write) before each batch"},
+            "mixed": out["mixed"], "fp64_path": out["fp64"],
+            "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_sequential_lj13(args):
+    """One FP64 walker of LJ13 (cube side 2.0 sigma, K=1, 200 BH steps in one
+    launch, step 0.4 sigma adapted every 10 steps toward 50%, kT=0.8): BH
+    steps per second on the GPU and with the oracle on one host core.  This
+    is a latency-bound case; the GPU is not expected to win it."""
+    import torch
+    from paper_2510_25938_gb300 import build as B
+    B.build()
+    from paper_2510_25938_gb300 import inputs as I
+    from paper_2510_25938_gb300 import lj_bh as L
+    import oracle as O
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    seed = I.workload_seed(0)
+    x0 = I.cube_starts(1, 13, 2.0, seed)
+    xm, em, _, _, _ = O.lbfgs_batch(x0, 1, uniform_n=13)
+    ctx = L.Ctx(0)
+    n_steps = 200
+
+    def state():
+        x = torch.as_tensor(xm.reshape(1, -1), dtype=torch.float64, device=dev)
+        return {"x_cur": x.clone(), "e_cur": torch.as_tensor(em, device=dev),
+                "x_best": x.clone(), "e_best": torch.as_tensor(em, device=dev),
+                "stepsize": torch.full((1,), 0.4, dtype=torch.float64, device=dev),
+                "win_accept": torch.zeros(1, dtype=torch.int32, device=dev),
+                "n_accept": torch.zeros(1, dtype=torch.int32, device=dev)}
+    p = L.BhParams(K=1, kT=0.8, seed=seed, n_steps=n_steps, min=L.LbfgsParams(prec=L.LJ_PREC_FP64))
+    times = []
+    for rep in range(max(args.warmup, 1) + args.steps):
+        st = state()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        L.bh_step_batched(ctx, st, p)
+        ev1.record()
+        torch.cuda.synchronize()
+        if rep >= max(args.warmup, 1):
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+    t = sum(times) / len(times)
+    ost = {"x_cur": xm.reshape(1, -1).copy(), "e_cur": em.copy(), "x_best": xm.reshape(1, -1).copy(),
+           "e_best": em.copy(), "stepsize": np.full(1, 0.4), "win_accept": np.zeros(1, np.int32),
+           "n_accept": np.zeros(1, np.int32)}
+    t0 = time.perf_counter()
+    O.bh_run(ost, O.BhParamsPy(K=1, kT=0.8, seed=seed, n_steps=n_steps))
+    t_cpu = time.perf_counter() - t0
+    line = {"metric": "BH steps/s", "value": n_steps / t, "unit": "BH steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "LJ13, one walker, K=1, 200 BH steps in one launch, FP64, "
+                                   "cube start side 2.0 sigma, kT=0.8, step 0.4 sigma"},
+            "ms_per_200_steps": 1e3 * t,
+            "cpu_oracle_one_core": {"value": n_steps / t_cpu, "unit": "BH steps/s", "cores": 1}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in BATCH_WORKLOADS:
+        return run_batch_workload(args)
+    if args.workload == "lj13-seq":
+        return run_sequential_lj13(args)
     return run_cuda(args)
 
 

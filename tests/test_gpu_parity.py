@@ -313,6 +313,39 @@ def test_minimise_cube_starts(lj, ctx, prec, n_atoms, side, cfg):
         assert diff <= 3 * se
 
 
+# large clusters: perturbed fcc fragments (0.1 sigma jitter), m = 20; the GPU
+# minimises a batch, the oracle the first candidates of it
+LARGE_CASES = [(500, 12, 2), (1000, 6, 1)]
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("n_atoms,n_cand,n_oracle", LARGE_CASES)
+def test_minimise_large_fcc(lj, ctx, prec, n_atoms, n_cand, n_oracle):
+    """The large-cluster workload at test scale (its candidates are the same
+    kind of start; the batch is smaller): every GPU minimum is checked for
+    validity (FP64 gradient and energy recomputed here), the sampled ones
+    against the oracle's minimum of the same start."""
+    x0 = I.fcc_fragments(n_cand, n_atoms, 0.1, I.workload_seed(4) + n_atoms)
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, uniform_n=n_atoms, prec=prec, m=20)
+    assert stats["minimisations"] == n_cand
+    assert (sg == O.CONVERGED).all(), sg
+    off = np.arange(n_cand + 1) * n_atoms
+    for c in range(n_cand):
+        a0, a1 = 3 * off[c], 3 * off[c + 1]
+        e_chk, g_chk = numpy_energy_grad(xg[a0:a1])
+        assert np.abs(g_chk).max() < GTOL * 1.01, c
+        assert abs(e_chk - eg[c]) <= 1e-9 * abs(eg[c]), c
+    xo, eo, so, _, _ = O.lbfgs_batch(x0[:n_oracle], n_oracle, uniform_n=n_atoms,
+                                     params=O.MinParams(m=20))
+    off_o = off[:n_oracle + 1]
+    if prec == 0:
+        _compare_minima(x0[:n_oracle].reshape(-1), off_o, xg[:3 * n_atoms * n_oracle],
+                        eg[:n_oracle], sg[:n_oracle], xo, eo, so, 0.0, FP64_REL_E, 1.0)
+    else:
+        _compare_minima(x0[:n_oracle].reshape(-1), off_o, xg[:3 * n_atoms * n_oracle],
+                        eg[:n_oracle], sg[:n_oracle], xo, eo, so, MIX_ABS_FINAL, 0.0, 1.0)
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 def test_minimise_bh_trial_moves_lj38(lj, ctx, prec):
     """Trial moves of the paper's kind (perturbations of minima by +-0.4
