@@ -237,7 +237,8 @@ lj_status lj_ctx_reserve(lj_ctx* ctx, int64_t max_cand, int32_t max_n, int32_t m
   if (max_n > LJ_MAX_ATOMS) return fail(ctx, LJ_ERR_UNSUPPORTED, "max_n > LJ_MAX_ATOMS");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
-  const int64_t slots = max_cand < 4 ? 4 : max_cand;
+  // persistent launches give whole CTAs of up to 4 teams one history slot each
+  const int64_t slots = max_cand < 4 ? 4 : (max_cand + 3) / 4 * 4;
   const size_t bytes = (size_t)slots * slot_bytes_bound(max_n < 1 ? 1 : max_n, max_m);
   ctx->reserved = false;
   lj_status st = ensure_ws(ctx, bytes);
