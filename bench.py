@@ -486,10 +486,13 @@ def run_batch_workload(args):
         uniform = w["n_lo"]
     n_cand = w["n_cand"]
     ctx = L.Ctx(0)
+    tuned = {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     offd = torch.as_tensor(off, device=dev) if off is not None else None
     out = {}
     for prec, name in ((L.LJ_PREC_MIXED, "mixed"), (L.LJ_PREC_FP64, "fp64")):
+        # threads per candidate chosen per size bucket by the library's autotuner
+        tuned[name] = ctx.autotune(w["n_hi"], w["m"], prec)
         times, conv = [], 0
         for rep in range(max(args.warmup, 1) + args.steps):
             x = torch.as_tensor(x0, dtype=torch.float64, device=dev).contiguous()
@@ -516,6 +519,7 @@ def run_batch_workload(args):
             "data": "synthetic", "config": {"workload": w["desc"], "precision": "mixed",
                                             "l2": "flushed (256 MiB write) before each batch"},
             "mixed": out["mixed"], "fp64_path": out["fp64"],
+            "autotuned_team_per_bucket": tuned,
             "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"]}
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -174,13 +174,16 @@ typedef struct {
 typedef enum {
     LJ_OPT_BH_TEAM = 1,      /* threads per candidate in bh_step_batched for
                                 clusters of <= 64 atoms: 0 (automatic), 32, 64, 128 */
-    LJ_OPT_LBFGS_TEAM = 2,   /* the same for lbfgs_minimize_batched */
-    LJ_OPT_F32_HANDOVER = 3, /* MIXED: the FP32 phase hands over once the predicted
-                                decrease -alpha phi'(0) falls below this many FP32
-                                ulps of |E| (1..4096; 0 = default 4) */
-    LJ_OPT_DF_HANDOVER = 4   /* MIXED: the double-float polish hands over to FP64
-                                once the predicted decrease falls below this many
-                                2^-48 |E| (1..65536; 0 = default 32) */
+    LJ_OPT_LBFGS_TEAM = 2,   /* threads per candidate in lbfgs_minimize_batched, all
+                                sizes: 0 (automatic or autotuned), 32, 64, 128, 256,
+                                512; a size too small for a bucket (more than two
+                                atoms per thread) falls back to the default there */
+    LJ_OPT_F32_HANDOVER = 3, /* MIXED: below this many FP32 ulps of |E| of predicted
+                                decrease -alpha phi'(0), the FP32 phase accepts
+                                steps on the gradient alone (1..4096; 0 = default 4) */
+    LJ_OPT_DF_HANDOVER = 4   /* MIXED: below this many 2^-48 |E| of predicted
+                                decrease, the double-float polish accepts steps on
+                                the gradient alone (1..65536; 0 = default 32) */
 } lj_option;
 
 const char* lj_status_string(lj_status s);
@@ -241,6 +244,32 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
  */
 lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_params* p,
                           const lj_bh_trace* trace, lj_stats* d_stats, void* stream);
+
+/*
+ * lj_ctx_autotune -- choose, per size bucket, the threads per candidate that
+ * lbfgs_minimize_batched uses on this ctx.  (A tuning aid of this library,
+ * not part of the paper's method.)
+ *   Buckets: N <= 32, 64, 128, 256, 512, 1024 atoms (LJ_TUNE_BUCKETS), the
+ *   same size classes an uneven batch is split into.  For every bucket up to
+ *   the one holding max_n, each team size the bucket can take (32..512
+ *   threads, one or two atoms per thread) minimises the same batch of
+ *   synthetic cube starts (reduced density 0.3, three quarters of the
+ *   bucket's upper size, history m, precision prec) twice; the second,
+ *   timed run decides by converged minimisations per second.
+ *   out_team  [LJ_TUNE_BUCKETS] chosen team sizes, 0 beyond max_n's bucket
+ *             (may be NULL).
+ * Later lbfgs_minimize_batched calls on this ctx use the chosen sizes unless
+ * LJ_OPT_LBFGS_TEAM is set (the option wins).  A setup call: it allocates
+ * and frees device memory, may enlarge the ctx workspace and synchronises
+ * `stream` -- call it before lj_ctx_reserve and outside graph capture.  It
+ * takes from well under a second (small max_n) to a few seconds (1024).
+ * Errors: INVALID_ARG (max_n < 2, m outside 1..LJ_MAX_M, prec FP32),
+ * UNSUPPORTED (max_n > LJ_MAX_ATOMS), CUDA.  On error the ctx keeps its
+ * previous choices.
+ */
+#define LJ_TUNE_BUCKETS 6
+lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec,
+                          int32_t* out_team, void* stream);
 
 /*
  * lbfgs_minimize_batched_noalloc -- the same minimisation as

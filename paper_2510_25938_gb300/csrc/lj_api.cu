@@ -24,6 +24,7 @@ struct lj_ctx {
   unsigned long long* queue = nullptr; // persistent-kernel work counter
   int bh_team = 0;                     // LJ_OPT_BH_TEAM (0 = automatic)
   int lbfgs_team = 0;                  // LJ_OPT_LBFGS_TEAM (0 = automatic)
+  int tune_team[ljh::kMaxBuckets] = {};  // lj_ctx_autotune: team per size bucket (0 = none)
   int f32_handover = 4;                // LJ_OPT_F32_HANDOVER (FP32 ulps of |E|)
   int df_handover = 32;                // LJ_OPT_DF_HANDOVER (2^-48 |E| units)
   std::string last_error;
@@ -150,6 +151,15 @@ lj_status check_min(lj_ctx* ctx, const lj_lbfgs_params* p) {
   return LJ_OK;
 }
 
+// size buckets of uneven batches (upper bounds, atoms); the autotuner keeps one
+// team size per bucket
+constexpr int kBound[ljh::kMaxBuckets] = {32, 64, 128, 256, 512, 1024};
+int bucket_of(int n) {
+  int b = 0;
+  while (b < ljh::kMaxBuckets - 1 && n > kBound[b]) ++b;
+  return b;
+}
+
 ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p) {
   ljh::MinParamsH h;
   h.f32_resolution = ctx->f32_handover * 5.9604644775390625e-8;    // ulps of 2^-24
@@ -254,8 +264,11 @@ lj_status lj_ctx_set_option(lj_ctx* ctx, lj_option opt, int64_t value) {
   switch (opt) {
     case LJ_OPT_BH_TEAM:
     case LJ_OPT_LBFGS_TEAM:
-      if (value != 0 && value != 32 && value != 64 && value != 128)
-        return fail(ctx, LJ_ERR_INVALID_ARG, "team size must be 0 (automatic), 32, 64 or 128");
+      if (opt == LJ_OPT_BH_TEAM && value != 0 && value != 32 && value != 64 && value != 128)
+        return fail(ctx, LJ_ERR_INVALID_ARG, "BH team size must be 0 (automatic), 32, 64 or 128");
+      if (opt == LJ_OPT_LBFGS_TEAM && value != 0 && value != 32 && value != 64 && value != 128 &&
+          value != 256 && value != 512)
+        return fail(ctx, LJ_ERR_INVALID_ARG, "L-BFGS team size must be 0, 32, 64, 128, 256 or 512");
       (opt == LJ_OPT_BH_TEAM ? ctx->bh_team : ctx->lbfgs_team) = (int)value;
       return LJ_OK;
     case LJ_OPT_F32_HANDOVER:
@@ -329,16 +342,14 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
   const int mixed = p->prec == LJ_PREC_MIXED;
   auto plan_for = [&](int bound, ljh::Plan* pl) {
-    return mixed ? ljh::lbfgs_plan_mixed(bound, p->m, batch->n_cand, ctx->device,
-                                         ctx->lbfgs_team, pl)
-                 : ljh::lbfgs_plan_fp64(bound, p->m, batch->n_cand, ctx->device,
-                                        ctx->lbfgs_team, pl);
+    const int team = ctx->lbfgs_team ? ctx->lbfgs_team : ctx->tune_team[bucket_of(bound)];
+    return mixed ? ljh::lbfgs_plan_mixed(bound, p->m, batch->n_cand, ctx->device, team, pl)
+                 : ljh::lbfgs_plan_fp64(bound, p->m, batch->n_cand, ctx->device, team, pl);
   };
   if (batch->uniform_n == 0 && max_n > 32 && batch->n_cand > 1) {
     // Uneven batch spanning several size classes: sort candidates into size
     // buckets on the device and drain each bucket with the team shape made
     // for it (one persistent launch per bucket, counts never leave the GPU).
-    static const int kBound[ljh::kMaxBuckets] = {32, 64, 128, 256, 512, 1024};
     int nb = 1;
     while (nb < ljh::kMaxBuckets && kBound[nb - 1] < max_n) ++nb;
     ljh::Buckets bk;
@@ -475,6 +486,110 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   return LJ_OK;
 }
 
+lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec,
+                          int32_t* out_team, void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  if (max_n < 2 || m < 1 || m > LJ_MAX_M || (prec != LJ_PREC_FP64 && prec != LJ_PREC_MIXED))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "autotune: max_n >= 2, 1 <= m <= LJ_MAX_M, FP64 or MIXED");
+  if (max_n > LJ_MAX_ATOMS) return fail(ctx, LJ_ERR_UNSUPPORTED, "max_n > LJ_MAX_ATOMS");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  // team sizes a bucket can take (A = ceil(N / T) <= 2), and the tuning batch
+  static const int kChoices[ljh::kMaxBuckets][3] = {
+      {32, 0, 0}, {32, 64, 128}, {64, 128, 0}, {128, 256, 0}, {256, 512, 0}, {512, 0, 0}};
+  static const int kTuneCand[ljh::kMaxBuckets] = {4096, 4096, 2048, 1024, 512, 304};
+  const int nb = bucket_of(max_n) + 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int saved_team = ctx->lbfgs_team;
+  const bool saved_reserved = ctx->reserved;
+  ctx->reserved = false;                  // tuning batches may grow the workspace
+  double* x = nullptr;
+  double* x0 = nullptr;
+  double* e = nullptr;
+  lj_stats* st = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  lj_status rc = LJ_OK;
+  int best_team[ljh::kMaxBuckets] = {};
+  auto cleanup = [&]() {
+    cudaFree(x); cudaFree(x0); cudaFree(e); cudaFree(st);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ctx->lbfgs_team = saved_team;
+    ctx->reserved = saved_reserved;
+  };
+  size_t max_x = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int nt = std::min(kBound[b], max_n) * 3 / 4 + 1;
+    max_x = std::max(max_x, (size_t)kTuneCand[b] * 3 * nt);
+  }
+  if (cudaMalloc(&x, max_x * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&x0, max_x * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&e, 4096 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&st, sizeof(lj_stats)) != cudaSuccess ||
+      cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) {
+    cleanup();
+    return fail(ctx, LJ_ERR_CUDA, "autotune: allocation failed");
+  }
+  lj_lbfgs_params p;
+  p.m = m; p.gtol = 1e-6; p.max_iter = 15000; p.max_ls = 20; p.c1 = 1e-3; p.c2 = 0.9;
+  p.alpha_max = 1e10; p.prec = prec; p.switch_gtol = 1e-3; p.deadline_cycles = 0;
+  p.eps = 1.0; p.sigma = 1.0;
+  for (int b = 0; b < nb && rc == LJ_OK; ++b) {
+    // a representative size of the bucket: three quarters of its upper end
+    const int nt = std::min(kBound[b], max_n) * 3 / 4 + 1;
+    const int64_t nc = kTuneCand[b];
+    const double side = std::cbrt(nt / 0.3);        // cube starts at reduced density 0.3
+    if (ljh::tune_starts_launch(x0, nc, nt, side, 0x5eedULL + b, s) != cudaSuccess) {
+      rc = fail(ctx, LJ_ERR_CUDA, "autotune: start generation failed");
+      break;
+    }
+    double best = -1.0;
+    for (int k = 0; k < 3 && kChoices[b][k]; ++k) {
+      const int team = kChoices[b][k];
+      if (kChoices[b][1] == 0) {             // a single choice: nothing to measure
+        best_team[b] = team;
+        break;
+      }
+      ctx->lbfgs_team = team;
+      lj_batch bt;
+      bt.n_cand = nc; bt.uniform_n = nt; bt.d_atom_offset = nullptr; bt.max_n = nt;
+      double tbest = 0.0;
+      unsigned long long conv = 0;
+      for (int rep = 0; rep < 2 && rc == LJ_OK; ++rep) {   // the first run is a warm-up
+        cudaMemcpyAsync(x, x0, (size_t)nc * 3 * nt * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(st, 0, sizeof(lj_stats), s);
+        cudaEventRecord(ev0, s);
+        rc = lbfgs_minimize_batched(ctx, &bt, &p, x, e, nullptr, nullptr, nullptr, st, stream);
+        cudaEventRecord(ev1, s);
+        if (rc != LJ_OK) break;
+        if (cudaEventSynchronize(ev1) != cudaSuccess) {
+          rc = fail(ctx, LJ_ERR_CUDA, "autotune: tuning run failed");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        lj_stats hs;
+        cudaMemcpy(&hs, st, sizeof(lj_stats), cudaMemcpyDeviceToHost);
+        tbest = ms;
+        conv = hs.converged;
+      }
+      if (rc != LJ_OK) break;
+      const double rate = tbest > 0.0 ? (double)conv / tbest : 0.0;
+      if (rate > best) {
+        best = rate;
+        best_team[b] = team;
+      }
+    }
+  }
+  cleanup();
+  if (rc != LJ_OK) return rc;
+  for (int b = 0; b < ljh::kMaxBuckets; ++b) {
+    ctx->tune_team[b] = b < nb ? best_team[b] : 0;
+    if (out_team) out_team[b] = ctx->tune_team[b];
+  }
+  return LJ_OK;
+}
+
 lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_params* p,
                                          double* d_x, double* d_energy, int32_t* d_status,
                                          int32_t* d_iters, int32_t* d_nevals, lj_stats* d_stats,
@@ -511,7 +626,6 @@ lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_p
   unsigned char* hist = base + kNoallocQueueBytes + list_bytes;
   const size_t avail = LJ_NOALLOC_SCRATCH_BYTES - kNoallocQueueBytes - list_bytes;
   // same bucketing as lbfgs_minimize_batched, so both give the same results
-  static const int kBound[ljh::kMaxBuckets] = {32, 64, 128, 256, 512, 1024};
   int nb = 1;
   ljh::Buckets bk;
   if (bucketed) {

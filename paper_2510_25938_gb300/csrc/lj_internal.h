@@ -103,6 +103,9 @@ cudaError_t lbfgs_launch_mixed(const LbfgsArgs& a, const Plan& plan, cudaStream_
 // sort candidates of an uneven batch into size buckets (device, no sync)
 cudaError_t bucketize_launch(const int64_t* off, int64_t n_cand, int nb, const Buckets& bk,
                              unsigned* counts, int* lists, cudaStream_t s);
+// autotuner inputs: n_cand uniform cube starts of n atoms, side `side` (device)
+cudaError_t tune_starts_launch(double* x, int64_t n_cand, int n, double side, uint64_t seed,
+                               cudaStream_t s);
 cudaError_t bh_plan_fp64(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
 cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
 cudaError_t bh_launch_fp64(const BhArgs& a, const Plan& plan, cudaStream_t s);

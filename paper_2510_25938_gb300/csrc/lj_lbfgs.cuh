@@ -160,9 +160,40 @@ namespace ljlb {
 // LJ_OPT_LBFGS_TEAM (32 / 64 / 128 threads) for clusters of up to 64 atoms.
 template <class F>
 cudaError_t dispatch_lb(int max_n, int team, F&& f) {
+  // team = 0: the default shape for max_n; otherwise `team` threads per
+  // candidate with A = ceil(max_n / team) atoms per thread when A <= 2 (a
+  // team too small for max_n falls back to the default)
   using std::integral_constant;
-  if (max_n <= 64 && team == 64) return f(integral_constant<int, 64>{}, integral_constant<int, 1>{});
-  if (max_n <= 64 && team == 128) return f(integral_constant<int, 128>{}, integral_constant<int, 1>{});
+  switch (team) {
+    case 32:
+      if (max_n <= 32) return f(integral_constant<int, 32>{}, integral_constant<int, 1>{});
+      if (max_n <= 64) return f(integral_constant<int, 32>{}, integral_constant<int, 2>{});
+      break;
+    case 64:
+      if (max_n <= 64) return f(integral_constant<int, 64>{}, integral_constant<int, 1>{});
+      if (max_n <= 128) return f(integral_constant<int, 64>{}, integral_constant<int, 2>{});
+      break;
+    case 128:
+      if (max_n <= 128) return f(integral_constant<int, 128>{}, integral_constant<int, 1>{});
+      if (max_n <= 256) return f(integral_constant<int, 128>{}, integral_constant<int, 2>{});
+      break;
+    case 256:
+      if (max_n <= 256) return f(integral_constant<int, 256>{}, integral_constant<int, 1>{});
+      if (max_n <= 512) return f(integral_constant<int, 256>{}, integral_constant<int, 2>{});
+      break;
+    case 512:
+      if (max_n <= 512) return f(integral_constant<int, 512>{}, integral_constant<int, 1>{});
+      if (max_n <= 1024) return f(integral_constant<int, 512>{}, integral_constant<int, 2>{});
+      break;
+    default:
+      // measured on GB300 (uneven cube starts, mixed and FP64 alike): one atom
+      // per thread beats two up to 128 atoms
+      if (max_n > 32 && max_n <= 64)
+        return f(integral_constant<int, 64>{}, integral_constant<int, 1>{});
+      if (max_n > 64 && max_n <= 128)
+        return f(integral_constant<int, 128>{}, integral_constant<int, 1>{});
+      break;
+  }
   return dispatch_team(max_n, f);
 }
 

@@ -21,9 +21,31 @@ __global__ void bucketize_kernel(const int64_t* __restrict__ off, long long n_ca
   }
 }
 
+// Synthetic starts for the autotuner: coordinate q of candidate c uniform
+// in [0, side), draw q of a Philox stream of its own (tag 5, counter (q, c)).
+__global__ void tune_starts_kernel(double* __restrict__ x, long long n_cand, int n3, double side,
+                                   unsigned long long seed) {
+  const long long total = n_cand * n3;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / n3;
+    const int q = (int)(i - c * n3);
+    x[i] = side * ljd::stream_u01(seed, 5u, (uint32_t)q, (uint32_t)c, 0u, 0u);
+  }
+}
+
 }  // namespace ljlb
 
 namespace ljh {
+
+cudaError_t tune_starts_launch(double* x, int64_t n_cand, int n, double side, uint64_t seed,
+                               cudaStream_t s) {
+  const long long total = n_cand * 3 * n;
+  const long long blocks = (total + 255) / 256;
+  ljlb::tune_starts_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(
+      x, n_cand, 3 * n, side, seed);
+  return cudaGetLastError();
+}
 
 cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int team, Plan* out) {
   return ljlb::plan_impl<false>(max_n, m, n_cand, device, team, out);

@@ -25,6 +25,7 @@ LJ_PREC_FP64, LJ_PREC_FP32, LJ_PREC_MIXED = 0, 1, 2
  LJ_CAND_TIMEOUT, LJ_CAND_BAD_INPUT) = range(6)
 LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 16
 LJ_OPT_BH_TEAM, LJ_OPT_LBFGS_TEAM, LJ_OPT_F32_HANDOVER, LJ_OPT_DF_HANDOVER = 1, 2, 3, 4
+LJ_TUNE_BUCKETS = 6
 STATS_FIELDS = ("evals32", "evals64", "evals_df", "iters32", "iters64", "pairs32", "pairs64",
                 "pairs_df", "vec_elems32", "vec_elems64", "converged", "minimisations",
                 "cycles32", "cycles_df", "cycles64", "cycles_direction", "cycles_linesearch")
@@ -110,6 +111,9 @@ def load():
             lib.lbfgs_minimize_batched_noalloc.argtypes = [C.POINTER(_Batch), C.POINTER(_Lbfgs),
                                                            P, P, P, P, P, P, P]
             lib.lbfgs_minimize_batched_noalloc.restype = C.c_int
+            lib.lj_ctx_autotune.argtypes = [P, C.c_int32, C.c_int32, C.c_int,
+                                            C.POINTER(C.c_int32), P]
+            lib.lj_ctx_autotune.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -158,6 +162,14 @@ class Ctx:
     def set_option(self, opt: int, value: int):
         """lj_ctx_set_option: e.g. set_option(LJ_OPT_BH_TEAM, 64)."""
         _check(self, load().lj_ctx_set_option(self.handle, opt, value), "lj_ctx_set_option")
+
+    def autotune(self, max_n: int, m: int = 10, prec: int = 2, stream=None) -> list:
+        """lj_ctx_autotune: the team size chosen for each of the LJ_TUNE_BUCKETS
+        size buckets (0 beyond max_n's bucket)."""
+        out = (C.c_int32 * LJ_TUNE_BUCKETS)()
+        _check(self, load().lj_ctx_autotune(self.handle, max_n, m, prec, out, _stream(stream)),
+               "lj_ctx_autotune")
+        return list(out)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -346,6 +346,31 @@ def test_minimise_large_fcc(lj, ctx, prec, n_atoms, n_cand, n_oracle):
                         eg[:n_oracle], sg[:n_oracle], xo, eo, so, MIX_ABS_FINAL, 0.0, 1.0)
 
 
+def test_autotune_then_uneven_batch(lj):
+    """lj_ctx_autotune picks a valid team size per bucket up to max_n; the
+    tuned ctx then minimises an uneven batch to valid minima."""
+    c = lj.Ctx(0)
+    table = c.autotune(150, 10, lj.LJ_PREC_MIXED)
+    # N = 150 falls in the <= 256 bucket: four buckets tuned
+    assert table[0] == 32 and table[1] in (32, 64, 128) and table[2] in (64, 128)
+    assert table[3] in (128, 256) and table[4:] == [0, 0]
+    sizes = I.uneven_sizes(64, 13, 150, I.workload_seed(3) + 31)
+    x0, off = I.uneven_cube_starts(sizes, 0.3, I.workload_seed(3) + 32)
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, c, x0, off=off, prec=2)
+    assert (sg == O.CONVERGED).mean() >= 0.95
+    for k in range(off.size - 1):
+        a0, a1 = 3 * off[k], 3 * off[k + 1]
+        e_chk, g_chk = numpy_energy_grad(xg[a0:a1])
+        if sg[k] == O.CONVERGED:
+            assert np.abs(g_chk).max() < GTOL * 1.01, k
+        assert abs(e_chk - eg[k]) <= 1e-9 * abs(eg[k]), k
+    with pytest.raises(lj.LjError):
+        c.autotune(1, 10, lj.LJ_PREC_MIXED)
+    with pytest.raises(lj.LjError):
+        c.autotune(100, 10, lj.LJ_PREC_FP32)
+    c.close()
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 def test_minimise_bh_trial_moves_lj38(lj, ctx, prec):
     """Trial moves of the paper's kind (perturbations of minima by +-0.4
