@@ -47,6 +47,10 @@ WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per BH step (512 L-
 PAIRS = N_ATOMS * (N_ATOMS - 1) // 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 (FMA) x max SM GHz
 FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of GB300
+# dram__bytes_read.sum + dram__bytes_write.sum of one bh_cluster_kernel launch of this
+# workload (ncu capture summarised in profiles/bh_cluster_kernel_lj38_64x8.md); set to
+# None whenever the kernel changes until it is captured again
+BH_DRAM_BYTES_PER_LAUNCH = 392192 + 5376
 
 
 def parse():
@@ -435,7 +439,9 @@ def run_cuda(args):
     if achieved_tf is not None:
         line["roofline"] = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                            "traffic": None, "kernel": "bh_cluster_kernel<64,1,mixed>",
+                            "traffic": BH_DRAM_BYTES_PER_LAUNCH,
+                            "traffic_unit": "DRAM bytes per launch (ncu)",
+                            "kernel": "bh_cluster_kernel<64,1,mixed>",
                             "fp64_flop_share": flops64 / flops if flops else None}
     if e2e:
         line["e2e"] = e2e
