@@ -40,6 +40,9 @@ sys.path.insert(0, ROOT)
 N_ATOMS, WALKERS, K = 38, 64, 8
 BH_PER_LAUNCH = 10          # BH steps per bench step (one adaptation window)
 SIDE, STEP0, KT = 3.2, 0.4, 0.8
+# MIXED precision policy parameter of this workload: the FP32 tier's gradient
+# threshold (swept on LJ38 BH: 1e-3 168k, 3e-4 179k, 1e-4 183k converged/s)
+SWITCH_GTOL = 1e-4
 CONFIG_ID = 1
 WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per BH step (512 L-BFGS "
             "minimisations per BH step), 10 BH steps per bench step, cube starts side "
@@ -306,7 +309,7 @@ def run_cuda(args):
     def timed_run(prec, n_steps, warmup):
         state = init_state()
         p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH, walker0=walker0,
-                       min=L.LbfgsParams(prec=prec))
+                       min=L.LbfgsParams(prec=prec, switch_gtol=SWITCH_GTOL))
         for s in range(warmup):
             p.step0 = s * BH_PER_LAUNCH
             L.bh_step_batched(ctx, state, p)
@@ -336,7 +339,7 @@ def run_cuda(args):
         dstate = init_state()
         host = {k: v.cpu().pin_memory() for k, v in dstate.items()}
         p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH, walker0=walker0,
-                       min=L.LbfgsParams(prec=prec))
+                       min=L.LbfgsParams(prec=prec, switch_gtol=SWITCH_GTOL))
         stats = L.new_stats(dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         for s in range(warmup + n_steps):
@@ -420,7 +423,7 @@ def run_cuda(args):
         "config": {"workload": WORKLOAD, "n_atoms": N_ATOMS, "walkers_per_gpu": WALKERS, "K": K,
                    "bh_steps_per_step": BH_PER_LAUNCH,
                    "minimisations_per_step": WALKERS * K * BH_PER_LAUNCH * world,
-                   "precision": "mixed",
+                   "precision": "mixed", "switch_gtol": SWITCH_GTOL,
                    "l2": "flushed (256 MiB write) between timed steps"},
         "minimisations_per_s": mins / t_dev,
         "converged_fraction": conv / max(mins, 1),

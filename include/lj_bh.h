@@ -106,7 +106,12 @@ typedef struct {
     double c1, c2;           /* strong-Wolfe constants (1e-3, 0.9) */
     double alpha_max;        /* largest trial step (1e10) */
     lj_precision prec;       /* LJ_PREC_FP64 or LJ_PREC_MIXED */
-    double switch_gtol;      /* MIXED: FP32 phase ends once ||g32||_inf < switch_gtol */
+    double switch_gtol;      /* MIXED: FP32 phase ends once ||g32||_inf < switch_gtol
+                                (1e-3 eps/sigma is a robust choice; the best value is
+                                workload-dependent, e.g. 1e-4 for LJ38 Basin Hopping;
+                                it must sit above the FP32 gradient noise, ~3e-5
+                                eps/sigma on LJ clusters, and a value below that costs
+                                up to 2000 FP32 iterations per minimisation) */
     int64_t deadline_cycles; /* > 0: a candidate still running after this many
                                 SM clock cycles stops with LJ_CAND_TIMEOUT */
     double eps, sigma;       /* LJ parameters of Eq. (1) (1, 1) */

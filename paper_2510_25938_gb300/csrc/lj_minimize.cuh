@@ -61,6 +61,11 @@ struct MinResult {
 
 enum : int { PH_CONVERGED = 0, PH_MAXITER = 1, PH_LSFAIL = 2, PH_SWITCH = 3, PH_TIMEOUT = 4 };
 
+// FP32-tier iterations after which gradient-only FP32 steps hand over: a
+// safety net for a switch_gtol below the FP32 gradient noise (~3e-5 eps/sigma
+// on LJ clusters); normal minimisations stay far below it
+constexpr int kFP32GradIters = 2000;
+
 // Precision policy of an L-BFGS tier.
 //   XP positions (float, double, or ff = double-float), XG gradient, V search
 //   directions and history, PM pair arithmetic (0: XP's own, 1: double-float).
@@ -508,6 +513,8 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 //   |E| (default 32 * 2^-48) its line searches accept steps on the gradient
 //   alone (approximate Wolfe conditions); hands over to FP64 when a line
 //   search fails.
+// In MODE 1, gradient-only steps past kFP32GradIters tier iterations also
+// hand over (a switch_gtol below the FP32 gradient noise).
 // ---------------------------------------------------------------------------
 template <int T, int A, typename P, int MODE>
 __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
@@ -860,6 +867,12 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
     team_max<T, 2, XG>(tm, mv);
     if (mv[0] < stop_gtol) return MODE == 1 ? PH_SWITCH : PH_CONVERGED;
     if (mv[1] > (XG)0) return PH_TIMEOUT;
+    if constexpr (MODE == 1) {
+      // a switch_gtol below the FP32 gradient noise would keep gradient-only
+      // FP32 steps iterating on noise: past kFP32GradIters iterations of the
+      // tier the double-float tier takes over
+      if (gmode && phase_iters >= kFP32GradIters) return PH_SWITCH;
+    }
   }
   return PH_MAXITER;
 }
