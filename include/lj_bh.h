@@ -106,12 +106,14 @@ typedef struct {
     double c1, c2;           /* strong-Wolfe constants (1e-3, 0.9) */
     double alpha_max;        /* largest trial step (1e10) */
     lj_precision prec;       /* LJ_PREC_FP64 or LJ_PREC_MIXED */
-    double switch_gtol;      /* MIXED: FP32 phase ends once ||g32||_inf < switch_gtol
-                                (1e-3 eps/sigma is a robust choice; the best value is
-                                workload-dependent, e.g. 1e-4 for LJ38 Basin Hopping;
-                                it must sit above the FP32 gradient noise, ~3e-5
-                                eps/sigma on LJ clusters, and a value below that costs
-                                up to 2000 FP32 iterations per minimisation) */
+    double switch_gtol;      /* MIXED: FP32 phase ends once ||g32||_inf < switch_gtol;
+                                0 = automatic: the value lj_ctx_autotune chose for the
+                                candidate's size bucket, else 1e-3.  The best value is
+                                workload-dependent (1e-4 for LJ38 Basin Hopping and for
+                                500-1000 atom fcc fragments, 1e-3 for <= 150-atom cube
+                                starts); it must sit above the FP32 gradient noise,
+                                ~3e-5 eps/sigma on LJ clusters, and a value below that
+                                costs up to 2000 FP32 iterations per minimisation) */
     int64_t deadline_cycles; /* > 0: a candidate still running after this many
                                 SM clock cycles stops with LJ_CAND_TIMEOUT */
     double eps, sigma;       /* LJ parameters of Eq. (1) (1, 1) */
@@ -252,19 +254,25 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_par
 
 /*
  * lj_ctx_autotune -- choose, per size bucket, the threads per candidate that
- * lbfgs_minimize_batched uses on this ctx.  (A tuning aid of this library,
- * not part of the paper's method.)
+ * lbfgs_minimize_batched uses on this ctx and, for MIXED, the FP32 tier's
+ * hand-over gradient.  (A tuning aid of this library, not part of the
+ * paper's method.)
  *   Buckets: N <= 32, 64, 128, 256, 512, 1024 atoms (LJ_TUNE_BUCKETS), the
  *   same size classes an uneven batch is split into.  For every bucket up to
  *   the one holding max_n, each team size the bucket can take (32..512
  *   threads, one or two atoms per thread) minimises the same batch of
  *   synthetic cube starts (reduced density 0.3, three quarters of the
  *   bucket's upper size, history m, precision prec) twice; the second,
- *   timed run decides by converged minimisations per second.
- *   out_team  [LJ_TUNE_BUCKETS] chosen team sizes, 0 beyond max_n's bucket
- *             (may be NULL).
- * Later lbfgs_minimize_batched calls on this ctx use the chosen sizes unless
- * LJ_OPT_LBFGS_TEAM is set (the option wins).  A setup call: it allocates
+ *   timed run decides by converged minimisations per second.  For MIXED the
+ *   same batch then runs with switch_gtol 1e-3, 3e-4 and 1e-4 on the chosen
+ *   team, and the fastest is kept.
+ *   out_team         [LJ_TUNE_BUCKETS] chosen team sizes, 0 beyond max_n's
+ *                    bucket (may be NULL).
+ *   out_switch_gtol  [LJ_TUNE_BUCKETS] chosen switch_gtol (MIXED), 0 beyond
+ *                    max_n's bucket or for FP64 (may be NULL).
+ * Later lbfgs_minimize_batched calls on this ctx use the chosen team sizes
+ * unless LJ_OPT_LBFGS_TEAM is set (the option wins), and the chosen
+ * switch_gtol wherever the call passes switch_gtol = 0.  A setup call: it allocates
  * and frees device memory, may enlarge the ctx workspace and synchronises
  * `stream` -- call it before lj_ctx_reserve and outside graph capture.  It
  * takes from well under a second (small max_n) to a few seconds (1024).
@@ -274,7 +282,21 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_par
  */
 #define LJ_TUNE_BUCKETS 6
 lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec,
-                          int32_t* out_team, void* stream);
+                          int32_t* out_team, double* out_switch_gtol, void* stream);
+
+/*
+ * lj_ctx_autotune_batch -- the same choice for one size bucket, measured on
+ * the caller's own starts: a uniform batch (uniform_n >= 1) whose first
+ * min(n_cand, max_sample) candidates of d_x (device, FP64, left unchanged)
+ * are minimised on copies with each choice.  Sets the entries of the bucket
+ * holding uniform_n; out_team / out_switch_gtol receive them (may be NULL).
+ * Use it when the workload's starts differ from random cube starts (e.g.
+ * perturbed lattice fragments).  Same setup-call rules and errors as
+ * lj_ctx_autotune; INVALID_ARG also for an uneven batch or max_sample < 1.
+ */
+lj_status lj_ctx_autotune_batch(lj_ctx* ctx, const lj_batch* batch, const double* d_x, int32_t m,
+                                lj_precision prec, int64_t max_sample, int32_t* out_team,
+                                double* out_switch_gtol, void* stream);
 
 /*
  * lbfgs_minimize_batched_noalloc -- the same minimisation as

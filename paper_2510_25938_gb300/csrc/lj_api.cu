@@ -25,6 +25,7 @@ struct lj_ctx {
   int bh_team = 0;                     // LJ_OPT_BH_TEAM (0 = automatic)
   int lbfgs_team = 0;                  // LJ_OPT_LBFGS_TEAM (0 = automatic)
   int tune_team[ljh::kMaxBuckets] = {};  // lj_ctx_autotune: team per size bucket (0 = none)
+  double tune_sg[ljh::kMaxBuckets] = {}; // ... and MIXED switch_gtol per bucket (0 = none)
   int f32_handover = 4;                // LJ_OPT_F32_HANDOVER (FP32 ulps of |E|)
   int df_handover = 32;                // LJ_OPT_DF_HANDOVER (2^-48 |E| units)
   std::string last_error;
@@ -144,8 +145,8 @@ lj_status check_min(lj_ctx* ctx, const lj_lbfgs_params* p) {
   if (!(p->alpha_max > 0.0)) return fail(ctx, LJ_ERR_INVALID_ARG, "alpha_max must be > 0");
   if (p->prec != LJ_PREC_FP64 && p->prec != LJ_PREC_MIXED)
     return fail(ctx, LJ_ERR_INVALID_ARG, "minimisation precision must be FP64 or MIXED");
-  if (p->prec == LJ_PREC_MIXED && !(p->switch_gtol > 0.0))
-    return fail(ctx, LJ_ERR_INVALID_ARG, "switch_gtol must be > 0");
+  if (p->prec == LJ_PREC_MIXED && !(p->switch_gtol >= 0.0))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "switch_gtol must be >= 0 (0: automatic)");
   if (!(p->eps > 0.0 && std::isfinite(p->eps) && p->sigma > 0.0 && std::isfinite(p->sigma)))
     return fail(ctx, LJ_ERR_INVALID_ARG, "eps and sigma must be finite and > 0");
   return LJ_OK;
@@ -160,13 +161,21 @@ int bucket_of(int n) {
   return b;
 }
 
-ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p) {
+// switch_gtol = 0 asks for the automatic value: the autotuned one of the
+// size bucket holding `bucket_n` atoms, else kDefaultSwitchGtol
+constexpr double kDefaultSwitchGtol = 1e-3;
+
+ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p, int bucket_n = 0) {
   ljh::MinParamsH h;
   h.f32_resolution = ctx->f32_handover * 5.9604644775390625e-8;    // ulps of 2^-24
   h.df_resolution = ctx->df_handover * 3.552713678800501e-15;      // units of 2^-48
   h.m = p->m; h.max_iter = p->max_iter; h.max_ls = p->max_ls;
   h.gtol = p->gtol; h.c1 = p->c1; h.c2 = p->c2; h.alpha_max = p->alpha_max;
   h.switch_gtol = p->switch_gtol; h.deadline = p->deadline_cycles;
+  if (!(h.switch_gtol > 0.0)) {
+    const double t = bucket_n > 0 ? ctx->tune_sg[bucket_of(bucket_n)] : 0.0;
+    h.switch_gtol = t > 0.0 ? t : kDefaultSwitchGtol;
+  }
   h.k = ljh::make_consts(p->eps, p->sigma);
   return h;
 }
@@ -378,7 +387,7 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
       a.uniform_n = 0;
       a.off = batch->d_atom_offset;
       a.max_n = bk.bound[b];
-      a.p = to_host(ctx, p);
+      a.p = to_host(ctx, p, bk.bound[b]);
       a.mixed = mixed;
       a.x = d_x;
       a.energy = d_energy;
@@ -408,7 +417,7 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   a.uniform_n = batch->uniform_n;
   a.off = batch->d_atom_offset;
   a.max_n = max_n;
-  a.p = to_host(ctx, p);
+  a.p = to_host(ctx, p, max_n);
   a.mixed = mixed;
   a.x = d_x;
   a.energy = d_energy;
@@ -486,107 +495,190 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   return LJ_OK;
 }
 
-lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec,
-                          int32_t* out_team, void* stream) {
-  if (!ctx) return LJ_ERR_INVALID_ARG;
-  if (max_n < 2 || m < 1 || m > LJ_MAX_M || (prec != LJ_PREC_FP64 && prec != LJ_PREC_MIXED))
-    return fail(ctx, LJ_ERR_INVALID_ARG, "autotune: max_n >= 2, 1 <= m <= LJ_MAX_M, FP64 or MIXED");
-  if (max_n > LJ_MAX_ATOMS) return fail(ctx, LJ_ERR_UNSUPPORTED, "max_n > LJ_MAX_ATOMS");
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
-  // team sizes a bucket can take (A = ceil(N / T) <= 2), and the tuning batch
-  static const int kChoices[ljh::kMaxBuckets][3] = {
-      {32, 0, 0}, {32, 64, 128}, {64, 128, 0}, {128, 256, 0}, {256, 512, 0}, {512, 0, 0}};
-  static const int kTuneCand[ljh::kMaxBuckets] = {4096, 4096, 2048, 1024, 512, 304};
-  const int nb = bucket_of(max_n) + 1;
-  cudaStream_t s = (cudaStream_t)stream;
-  const int saved_team = ctx->lbfgs_team;
-  const bool saved_reserved = ctx->reserved;
-  ctx->reserved = false;                  // tuning batches may grow the workspace
-  double* x = nullptr;
-  double* x0 = nullptr;
+}  // extern "C"
+
+namespace {
+
+// team sizes a bucket can take (A = ceil(N / T) <= 2), the synthetic tuning
+// batch per bucket, and the MIXED hand-over gradients tried
+constexpr int kTuneChoices[ljh::kMaxBuckets][3] = {
+    {32, 0, 0}, {32, 64, 128}, {64, 128, 0}, {128, 256, 0}, {256, 512, 0}, {512, 0, 0}};
+constexpr int kTuneCand[ljh::kMaxBuckets] = {4096, 4096, 2048, 1024, 512, 304};
+constexpr double kSgChoices[3] = {1e-3, 3e-4, 1e-4};
+
+// Device buffers and timing of one autotuning call; restores the ctx's team
+// option and reservation on destruction.
+struct Tuner {
+  lj_ctx* ctx;
+  cudaStream_t s;
+  void* stream;
+  double* x = nullptr;     // working copy minimised by each tuning run
+  double* x0 = nullptr;    // the tuning starts
   double* e = nullptr;
   lj_stats* st = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  lj_status rc = LJ_OK;
-  int best_team[ljh::kMaxBuckets] = {};
-  auto cleanup = [&]() {
+  int saved_team;
+  bool saved_reserved;
+  Tuner(lj_ctx* c, void* strm)
+      : ctx(c), s((cudaStream_t)strm), stream(strm), saved_team(c->lbfgs_team),
+        saved_reserved(c->reserved) {
+    ctx->reserved = false;                // tuning batches may grow the workspace
+  }
+  ~Tuner() {
     cudaFree(x); cudaFree(x0); cudaFree(e); cudaFree(st);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     ctx->lbfgs_team = saved_team;
     ctx->reserved = saved_reserved;
-  };
-  size_t max_x = 0;
-  for (int b = 0; b < nb; ++b) {
-    const int nt = std::min(kBound[b], max_n) * 3 / 4 + 1;
-    max_x = std::max(max_x, (size_t)kTuneCand[b] * 3 * nt);
   }
-  if (cudaMalloc(&x, max_x * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&x0, max_x * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&e, 4096 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&st, sizeof(lj_stats)) != cudaSuccess ||
-      cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) {
-    cleanup();
-    return fail(ctx, LJ_ERR_CUDA, "autotune: allocation failed");
+  lj_status alloc(size_t coords, int64_t n_cand) {
+    if (cudaMalloc(&x, coords * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&x0, coords * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&e, (size_t)n_cand * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&st, sizeof(lj_stats)) != cudaSuccess ||
+        cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess)
+      return fail(ctx, LJ_ERR_CUDA, "autotune: allocation failed");
+    return LJ_OK;
   }
-  lj_lbfgs_params p;
-  p.m = m; p.gtol = 1e-6; p.max_iter = 15000; p.max_ls = 20; p.c1 = 1e-3; p.c2 = 0.9;
-  p.alpha_max = 1e10; p.prec = prec; p.switch_gtol = 1e-3; p.deadline_cycles = 0;
-  p.eps = 1.0; p.sigma = 1.0;
-  for (int b = 0; b < nb && rc == LJ_OK; ++b) {
-    // a representative size of the bucket: three quarters of its upper end
-    const int nt = std::min(kBound[b], max_n) * 3 / 4 + 1;
-    const int64_t nc = kTuneCand[b];
-    const double side = std::cbrt(nt / 0.3);        // cube starts at reduced density 0.3
-    if (ljh::tune_starts_launch(x0, nc, nt, side, 0x5eedULL + b, s) != cudaSuccess) {
-      rc = fail(ctx, LJ_ERR_CUDA, "autotune: start generation failed");
-      break;
+  // converged minimisations per ms of the second of two runs on x0
+  lj_status rate(const lj_lbfgs_params& p, int64_t nc, int nt, int team, double* out) {
+    ctx->lbfgs_team = team;
+    lj_batch bt;
+    bt.n_cand = nc; bt.uniform_n = nt; bt.d_atom_offset = nullptr; bt.max_n = nt;
+    float ms = 0.f;
+    unsigned long long conv = 0;
+    for (int rep = 0; rep < 2; ++rep) {       // the first run is a warm-up
+      cudaMemcpyAsync(x, x0, (size_t)nc * 3 * nt * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cudaMemsetAsync(st, 0, sizeof(lj_stats), s);
+      cudaEventRecord(ev0, s);
+      lj_status rc = lbfgs_minimize_batched(ctx, &bt, &p, x, e, nullptr, nullptr, nullptr, st,
+                                            stream);
+      cudaEventRecord(ev1, s);
+      if (rc != LJ_OK) return rc;
+      if (cudaEventSynchronize(ev1) != cudaSuccess)
+        return fail(ctx, LJ_ERR_CUDA, "autotune: tuning run failed");
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      lj_stats hs;
+      if (cudaMemcpy(&hs, st, sizeof(lj_stats), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, LJ_ERR_CUDA, "autotune: reading statistics failed");
+      conv = hs.converged;
     }
-    double best = -1.0;
-    for (int k = 0; k < 3 && kChoices[b][k]; ++k) {
-      const int team = kChoices[b][k];
-      if (kChoices[b][1] == 0) {             // a single choice: nothing to measure
-        best_team[b] = team;
+    *out = ms > 0.f ? (double)conv / ms : 0.0;
+    return LJ_OK;
+  }
+  // the team size, then (MIXED) the switch_gtol of bucket b on the starts in x0
+  lj_status bucket(int b, int64_t nc, int nt, int m, lj_precision prec, int* team, double* sg) {
+    lj_lbfgs_params p;
+    p.m = m; p.gtol = 1e-6; p.max_iter = 15000; p.max_ls = 20; p.c1 = 1e-3; p.c2 = 0.9;
+    p.alpha_max = 1e10; p.prec = prec; p.switch_gtol = kDefaultSwitchGtol;
+    p.deadline_cycles = 0; p.eps = 1.0; p.sigma = 1.0;
+    *team = kTuneChoices[b][0];
+    if (kTuneChoices[b][1] != 0) {
+      double best = -1.0;
+      for (int k = 0; k < 3 && kTuneChoices[b][k]; ++k) {
+        double r = 0.0;
+        lj_status rc = rate(p, nc, nt, kTuneChoices[b][k], &r);
+        if (rc != LJ_OK) return rc;
+        if (r > best) { best = r; *team = kTuneChoices[b][k]; }
+      }
+    }
+    *sg = 0.0;
+    if (prec == LJ_PREC_MIXED) {
+      double best = -1.0;
+      for (double v : kSgChoices) {
+        p.switch_gtol = v;
+        double r = 0.0;
+        lj_status rc = rate(p, nc, nt, *team, &r);
+        if (rc != LJ_OK) return rc;
+        if (r > best) { best = r; *sg = v; }
+      }
+    }
+    return LJ_OK;
+  }
+};
+
+lj_status check_tune_args(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec) {
+  if (max_n < 2 || m < 1 || m > LJ_MAX_M || (prec != LJ_PREC_FP64 && prec != LJ_PREC_MIXED))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "autotune: N >= 2, 1 <= m <= LJ_MAX_M, FP64 or MIXED");
+  if (max_n > LJ_MAX_ATOMS) return fail(ctx, LJ_ERR_UNSUPPORTED, "N > LJ_MAX_ATOMS");
+  return LJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec,
+                          int32_t* out_team, double* out_switch_gtol, void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  lj_status rc = check_tune_args(ctx, max_n, m, prec);
+  if (rc != LJ_OK) return rc;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  const int nb = bucket_of(max_n) + 1;
+  int team[ljh::kMaxBuckets] = {};
+  double sg[ljh::kMaxBuckets] = {};
+  {
+    Tuner tu(ctx, stream);
+    size_t max_x = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int nt = std::min(kBound[b], max_n) * 3 / 4 + 1;
+      max_x = std::max(max_x, (size_t)kTuneCand[b] * 3 * nt);
+    }
+    rc = tu.alloc(max_x, 4096);
+    for (int b = 0; b < nb && rc == LJ_OK; ++b) {
+      // a representative size of the bucket: three quarters of its upper end,
+      // cube starts at reduced density 0.3
+      const int nt = std::min(kBound[b], max_n) * 3 / 4 + 1;
+      if (ljh::tune_starts_launch(tu.x0, kTuneCand[b], nt, std::cbrt(nt / 0.3), 0x5eedULL + b,
+                                  tu.s) != cudaSuccess) {
+        rc = fail(ctx, LJ_ERR_CUDA, "autotune: start generation failed");
         break;
       }
-      ctx->lbfgs_team = team;
-      lj_batch bt;
-      bt.n_cand = nc; bt.uniform_n = nt; bt.d_atom_offset = nullptr; bt.max_n = nt;
-      double tbest = 0.0;
-      unsigned long long conv = 0;
-      for (int rep = 0; rep < 2 && rc == LJ_OK; ++rep) {   // the first run is a warm-up
-        cudaMemcpyAsync(x, x0, (size_t)nc * 3 * nt * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        cudaMemsetAsync(st, 0, sizeof(lj_stats), s);
-        cudaEventRecord(ev0, s);
-        rc = lbfgs_minimize_batched(ctx, &bt, &p, x, e, nullptr, nullptr, nullptr, st, stream);
-        cudaEventRecord(ev1, s);
-        if (rc != LJ_OK) break;
-        if (cudaEventSynchronize(ev1) != cudaSuccess) {
-          rc = fail(ctx, LJ_ERR_CUDA, "autotune: tuning run failed");
-          break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev0, ev1);
-        lj_stats hs;
-        cudaMemcpy(&hs, st, sizeof(lj_stats), cudaMemcpyDeviceToHost);
-        tbest = ms;
-        conv = hs.converged;
-      }
-      if (rc != LJ_OK) break;
-      const double rate = tbest > 0.0 ? (double)conv / tbest : 0.0;
-      if (rate > best) {
-        best = rate;
-        best_team[b] = team;
-      }
+      rc = tu.bucket(b, kTuneCand[b], nt, m, prec, &team[b], &sg[b]);
     }
   }
-  cleanup();
   if (rc != LJ_OK) return rc;
   for (int b = 0; b < ljh::kMaxBuckets; ++b) {
-    ctx->tune_team[b] = b < nb ? best_team[b] : 0;
+    ctx->tune_team[b] = b < nb ? team[b] : 0;
+    ctx->tune_sg[b] = b < nb ? sg[b] : 0.0;
     if (out_team) out_team[b] = ctx->tune_team[b];
+    if (out_switch_gtol) out_switch_gtol[b] = ctx->tune_sg[b];
   }
+  return LJ_OK;
+}
+
+lj_status lj_ctx_autotune_batch(lj_ctx* ctx, const lj_batch* batch, const double* d_x, int32_t m,
+                                lj_precision prec, int64_t max_sample, int32_t* out_team,
+                                double* out_switch_gtol, void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  if (!batch || !d_x || batch->uniform_n < 1 || batch->n_cand < 1 || max_sample < 1)
+    return fail(ctx, LJ_ERR_INVALID_ARG,
+                "autotune_batch: a uniform batch (uniform_n >= 1), d_x and max_sample >= 1");
+  lj_status rc = check_tune_args(ctx, batch->uniform_n, m, prec);
+  if (rc != LJ_OK) return rc;
+  if (!aligned(d_x, 8)) return fail(ctx, LJ_ERR_INVALID_ARG, "misaligned pointer");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  const int nt = batch->uniform_n;
+  const int b = bucket_of(nt);
+  const int64_t nc = std::min<int64_t>(batch->n_cand, max_sample);
+  int team = 0;
+  double sg = 0.0;
+  {
+    Tuner tu(ctx, stream);
+    rc = tu.alloc((size_t)nc * 3 * nt, nc);
+    if (rc == LJ_OK &&
+        cudaMemcpyAsync(tu.x0, d_x, (size_t)nc * 3 * nt * sizeof(double),
+                        cudaMemcpyDeviceToDevice, tu.s) != cudaSuccess)
+      rc = fail(ctx, LJ_ERR_CUDA, "autotune_batch: copying the sample failed");
+    if (rc == LJ_OK) rc = tu.bucket(b, nc, nt, m, prec, &team, &sg);
+  }
+  if (rc != LJ_OK) return rc;
+  ctx->tune_team[b] = team;
+  ctx->tune_sg[b] = sg;
+  if (out_team) *out_team = team;
+  if (out_switch_gtol) *out_switch_gtol = sg;
   return LJ_OK;
 }
 
@@ -658,7 +750,7 @@ lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_p
     a.uniform_n = batch->uniform_n;
     a.off = batch->d_atom_offset;
     a.max_n = bk.bound[b];
-    a.p = to_host(&kDefaults, p);
+    a.p = to_host(&kDefaults, p, bk.bound[b]);
     a.mixed = mixed;
     a.x = d_x;
     a.energy = d_energy;

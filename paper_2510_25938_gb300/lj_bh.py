@@ -112,8 +112,12 @@ def load():
                                                            P, P, P, P, P, P, P]
             lib.lbfgs_minimize_batched_noalloc.restype = C.c_int
             lib.lj_ctx_autotune.argtypes = [P, C.c_int32, C.c_int32, C.c_int,
-                                            C.POINTER(C.c_int32), P]
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_double), P]
             lib.lj_ctx_autotune.restype = C.c_int
+            lib.lj_ctx_autotune_batch.argtypes = [P, C.POINTER(_Batch), P, C.c_int32, C.c_int,
+                                                  C.c_int64, C.POINTER(C.c_int32),
+                                                  C.POINTER(C.c_double), P]
+            lib.lj_ctx_autotune_batch.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -163,13 +167,28 @@ class Ctx:
         """lj_ctx_set_option: e.g. set_option(LJ_OPT_BH_TEAM, 64)."""
         _check(self, load().lj_ctx_set_option(self.handle, opt, value), "lj_ctx_set_option")
 
-    def autotune(self, max_n: int, m: int = 10, prec: int = 2, stream=None) -> list:
-        """lj_ctx_autotune: the team size chosen for each of the LJ_TUNE_BUCKETS
-        size buckets (0 beyond max_n's bucket)."""
-        out = (C.c_int32 * LJ_TUNE_BUCKETS)()
-        _check(self, load().lj_ctx_autotune(self.handle, max_n, m, prec, out, _stream(stream)),
-               "lj_ctx_autotune")
-        return list(out)
+    def autotune(self, max_n: int, m: int = 10, prec: int = 2, stream=None) -> dict:
+        """lj_ctx_autotune: {"team": [...], "switch_gtol": [...]}, one entry per
+        LJ_TUNE_BUCKETS size bucket (0 beyond max_n's bucket)."""
+        team = (C.c_int32 * LJ_TUNE_BUCKETS)()
+        sg = (C.c_double * LJ_TUNE_BUCKETS)()
+        _check(self, load().lj_ctx_autotune(self.handle, max_n, m, prec, team, sg,
+                                            _stream(stream)), "lj_ctx_autotune")
+        return {"team": list(team), "switch_gtol": list(sg)}
+
+    def autotune_batch(self, x: torch.Tensor, n_cand: int, uniform_n: int, m: int = 10,
+                       prec: int = 2, max_sample: int = 1024, stream=None) -> dict:
+        """lj_ctx_autotune_batch on the caller's own uniform batch x (float64,
+        left unchanged): {"team": t, "switch_gtol": s} of the bucket of uniform_n."""
+        if x.dtype != torch.float64:
+            raise ValueError("x must be float64")
+        team = C.c_int32()
+        sg = C.c_double()
+        b = _Batch(n_cand, uniform_n, None, uniform_n)
+        _check(self, load().lj_ctx_autotune_batch(self.handle, C.byref(b), _ptr(x), m, prec,
+                                                  max_sample, C.byref(team), C.byref(sg),
+                                                  _stream(stream)), "lj_ctx_autotune_batch")
+        return {"team": team.value, "switch_gtol": sg.value}
 
     def close(self):
         if getattr(self, "handle", None):
@@ -194,7 +213,7 @@ class LbfgsParams:
     c2: float = 0.9
     alpha_max: float = 1e10
     prec: int = LJ_PREC_MIXED
-    switch_gtol: float = 1e-3
+    switch_gtol: float = 0.0       # 0: automatic (autotuned per bucket, else 1e-3)
     deadline_cycles: int = 0
     eps: float = 1.0
     sigma: float = 1.0

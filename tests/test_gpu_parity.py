@@ -350,7 +350,10 @@ def test_autotune_then_uneven_batch(lj):
     """lj_ctx_autotune picks a valid team size per bucket up to max_n; the
     tuned ctx then minimises an uneven batch to valid minima."""
     c = lj.Ctx(0)
-    table = c.autotune(150, 10, lj.LJ_PREC_MIXED)
+    tuned = c.autotune(150, 10, lj.LJ_PREC_MIXED)
+    table = tuned["team"]
+    assert all(v in (1e-3, 3e-4, 1e-4) for v in tuned["switch_gtol"][:4])
+    assert tuned["switch_gtol"][4:] == [0.0, 0.0]
     # N = 150 falls in the <= 256 bucket: four buckets tuned
     assert table[0] == 32 and table[1] in (32, 64, 128) and table[2] in (64, 128)
     assert table[3] in (128, 256) and table[4:] == [0, 0]
@@ -368,6 +371,29 @@ def test_autotune_then_uneven_batch(lj):
         c.autotune(1, 10, lj.LJ_PREC_MIXED)
     with pytest.raises(lj.LjError):
         c.autotune(100, 10, lj.LJ_PREC_FP32)
+    c.close()
+
+
+def test_autotune_batch_on_own_starts(lj):
+    """lj_ctx_autotune_batch tunes the bucket of a uniform batch on copies of
+    the caller's starts (left unchanged) and the tuned ctx then minimises it."""
+    c = lj.Ctx(0)
+    n_cand, n_atoms = 96, 100
+    x0 = I.fcc_fragments(n_cand, n_atoms, 0.1, I.workload_seed(4) + 7)
+    xs = torch.as_tensor(x0.reshape(-1), dtype=torch.float64, device="cuda").contiguous()
+    keep = xs.clone()
+    t = c.autotune_batch(xs, n_cand, n_atoms, 10, lj.LJ_PREC_MIXED, max_sample=48)
+    assert t["team"] in (64, 128) and t["switch_gtol"] in (1e-3, 3e-4, 1e-4)
+    assert torch.equal(xs, keep)
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, c, x0, uniform_n=n_atoms, prec=2)
+    assert (sg == O.CONVERGED).all()
+    for k in range(n_cand):
+        e_chk, g_chk = numpy_energy_grad(xg[3 * n_atoms * k:3 * n_atoms * (k + 1)])
+        assert np.abs(g_chk).max() < GTOL * 1.01 and abs(e_chk - eg[k]) <= 1e-9 * abs(eg[k])
+    with pytest.raises(lj.LjError):
+        c.autotune_batch(xs, n_cand, n_atoms, 10, lj.LJ_PREC_MIXED, max_sample=0)
+    with pytest.raises(lj.LjError):
+        c.autotune_batch(xs, n_cand, n_atoms, 10, lj.LJ_PREC_FP32)
     c.close()
 
 
