@@ -35,6 +35,7 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
   p.gtol = h.gtol; p.c1 = h.c1; p.c2 = h.c2; p.alpha_max = h.alpha_max;
   p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.k = h.k;
   p.f32_resolution = h.f32_resolution; p.df_resolution = h.df_resolution;
+  p.tiled = 0;
   return p;
 }
 
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
   long long* word;
   carve_team<T>(sp, n, true, a.hist_on_chip ? a.hist_slot_bytes : 0, pos, hbuf, hist, tm.red,
                 word);
-  const MinParams p = to_dev(a.p);
+  MinParams p = to_dev(a.p);
+  p.tiled = n > kTileMinN;             // hbuf: pair buffer up to 64 atoms, tiles above 256
   if (!a.hist_on_chip)
     hist = static_cast<unsigned char*>(a.hist) + ((size_t)w * K + k) * a.hist_slot_bytes;
   const uint32_t wg = (uint32_t)(a.walker0 + w);

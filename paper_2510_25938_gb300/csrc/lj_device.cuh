@@ -550,4 +550,94 @@ __device__ __forceinline__ void pair_term_df(const PosDF& a, const PosDF& b, ff&
   vx = df_mul(c, dx); vy = df_mul(c, dy); vz = df_mul(c, dz);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float evaluation of clusters above the half-pair size: each
+// unordered pair once, in tiles of 32 x 32 atom blocks (block b = atoms
+// 32b .. 32b+31).  Blocks are paired by the circle method -- round r pairs
+// block NB-1 with r and (r+t) mod (NB-1) with (r-t) mod (NB-1), NB even
+// (a missing block when the count is odd) -- so that within a round every
+// block is in exactly one tile.  A warp takes a tile (I, J): lane l keeps
+// atom 32I+l, and atom 32J+l's position and reaction rotate one lane per
+// step, so after 32 steps every lane has met every atom of J and holds its
+// own J atom's reaction again.  Both sides are then added into per-atom
+// double-float accumulators acc[c * n + atom] in shared memory: within a
+// round no atom is in two tiles and rounds are separated by a barrier, so
+// there are no conflicts and the order is fixed.  A last round takes the
+// diagonal tiles (pairs inside a block, each once).  Positions are scaled by
+// 1/sigma; v = c (x_i - x_j) as in pair_term_df; e accumulates this lane's
+// pair energies s6 (s6 - 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ PosDF shfl_pos(const PosDF& q, int src) {
+  PosDF r;
+  r.xh = __shfl_sync(kFull, q.xh, src); r.yh = __shfl_sync(kFull, q.yh, src);
+  r.zh = __shfl_sync(kFull, q.zh, src); r.wh = 0.f;
+  r.xl = __shfl_sync(kFull, q.xl, src); r.yl = __shfl_sync(kFull, q.yl, src);
+  r.zl = __shfl_sync(kFull, q.zl, src); r.wl = 0.f;
+  return r;
+}
+__device__ __forceinline__ ff shfl_ff(ff v, int src) {
+  return ff{__shfl_sync(kFull, v.hi, src), __shfl_sync(kFull, v.lo, src)};
+}
+
+template <int T>
+__device__ void df_tile_eval(const Team<T>& tm, int n, const PosDF* __restrict__ pos, ff* acc,
+                             ff& e) {
+  constexpr int W = T / 32;
+  const int lane = tm.rank & 31, warp = tm.rank >> 5;
+  for (int i = tm.rank; i < 3 * n; i += T) acc[i] = ff{0.f, 0.f};
+  tm.sync();
+  const int nb = (n + 31) >> 5;
+  const int nbe = nb + (nb & 1);
+  const PosDF far{0x1p60f, 0x1p60f, 0x1p60f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  auto tile = [&](int I, int J) {
+    const bool diag = I == J;
+    const int i = 32 * I + lane;
+    const bool vi = i < n;
+    const PosDF pi = vi ? pos[i] : far;
+    int jl = 32 * J + lane;
+    PosDF pj = jl < n ? pos[jl] : far;
+    ff fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f};
+    ff hx{0.f, 0.f}, hy{0.f, 0.f}, hz{0.f, 0.f};   // reaction of the rotating J atom
+    const int src = (lane + 1) & 31;
+    for (int k = 0; k < 32; ++k) {
+      const int jk = 32 * J + ((lane + k) & 31);
+      bool act = vi && jk < n;
+      if (diag) act = act && k >= 1 && (k < 16 || (k == 16 && lane < 16));
+      if (__any_sync(kFull, act)) {
+        ff vx, vy, vz, ep;
+        pair_term_df(pi, pj, vx, vy, vz, ep);
+        if (act) {
+          fx = df_add(fx, vx); fy = df_add(fy, vy); fz = df_add(fz, vz);
+          hx = df_sub(hx, vx); hy = df_sub(hy, vy); hz = df_sub(hz, vz);
+          e = df_add(e, ep);
+        }
+      }
+      pj = shfl_pos(pj, src);
+      hx = shfl_ff(hx, src); hy = shfl_ff(hy, src); hz = shfl_ff(hz, src);
+    }
+    if (diag) {
+      fx = df_add(fx, hx); fy = df_add(fy, hy); fz = df_add(fz, hz);
+    } else if (jl < n) {
+      acc[jl] = df_add(acc[jl], hx);
+      acc[n + jl] = df_add(acc[n + jl], hy);
+      acc[2 * n + jl] = df_add(acc[2 * n + jl], hz);
+    }
+    if (vi) {
+      acc[i] = df_add(acc[i], fx);
+      acc[n + i] = df_add(acc[n + i], fy);
+      acc[2 * n + i] = df_add(acc[2 * n + i], fz);
+    }
+  };
+  for (int r = 0; r < nbe - 1; ++r) {
+    for (int t = warp; t < nbe / 2; t += W) {
+      const int I = t == 0 ? nbe - 1 : (r + t) % (nbe - 1);
+      const int J = t == 0 ? r : (r - t + nbe - 1) % (nbe - 1);
+      if (I < nb && J < nb) tile(I, J);
+    }
+    tm.sync();
+  }
+  for (int b = warp; b < nb; b += W) tile(b, b);
+  tm.sync();
+}
+
 }  // namespace ljd

@@ -19,11 +19,16 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
   p.gtol = h.gtol; p.c1 = h.c1; p.c2 = h.c2; p.alpha_max = h.alpha_max;
   p.switch_gtol = h.switch_gtol; p.deadline = h.deadline; p.k = h.k;
   p.f32_resolution = h.f32_resolution; p.df_resolution = h.df_resolution;
+  p.tiled = 0;
   return p;
 }
 
+// Register budget: teams for more than 256 atoms (which carry the tiled
+// double-float evaluation) are allowed all registers of one CTA per SM; the
+// others are left to the compiler's own occupancy choice.
 template <int T, int A, bool MIXED>
-__global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArgs a) {
+__global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
+    lbfgs_kernel(ljh::LbfgsArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int TPC = cta_threads_for(T) / T;
   const int team = threadIdx.x / T;
@@ -37,7 +42,8 @@ __global__ void __launch_bounds__(cta_threads_for(T)) lbfgs_kernel(ljh::LbfgsArg
   const size_t hb = a.hist_on_chip ? a.hist_slot_bytes : 0;
   carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true, hb), a.max_n, true, hb, pos,
                 hbuf, hist, tm.red, word);
-  const MinParams p = to_dev(a.p);
+  MinParams p = to_dev(a.p);
+  p.tiled = a.max_n > kTileMinN;       // hbuf: pair buffer up to 64 atoms, tiles above 256
   const long long slot = (long long)blockIdx.x * TPC + team;
   if (!a.hist_on_chip) hist = static_cast<unsigned char*>(a.hist) + slot * a.hist_slot_bytes;
 

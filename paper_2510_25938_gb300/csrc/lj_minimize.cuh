@@ -45,6 +45,7 @@ struct MinParams {
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
   ljh::LjConsts k;         // Eq. (1) constants from eps and sigma (host-derived)
+  int tiled;               // hbuf holds tile accumulators (teams for > 64 atoms), not pairs
   double f32_resolution;   // FP32 phase hands over below this predicted decrease / |E|
   double df_resolution;    // double-float polish hands over below this / |E|
 };
@@ -162,7 +163,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   tm.sync();
   V dp = (V)0;
   if constexpr (PM == 1 || std::is_same<X, double>::value) {
-    if (hbuf != nullptr) {
+    if (hbuf != nullptr && !p.tiled) {
       // ---- half-pair evaluation ---------------------------------------------
       // pair phase: thread `rank` takes pairs rank, rank + T, ...; two pairs
       // per iteration (the second one clamped to a valid pair and discarded
@@ -279,6 +280,30 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
     const PosDF* pos = static_cast<const PosDF*>(posv);
     const float gs = p.k.gs_f;
     ff e{0.f, 0.f};
+    // ---- tiled half-pair evaluation (teams for more than 256 atoms; compiled
+    // only for team shapes that can hold them) ------------------------------
+    if constexpr (T * A > 256) {
+    if (hbuf != nullptr && p.tiled) {
+      ff* acc = static_cast<ff*>(hbuf);
+      df_tile_eval<T>(tm, n, pos, acc, e);
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int i = tm.rank + a * T;
+        if (i < n) {
+          const ff sx = acc[i], sy = acc[n + i], sz = acc[2 * n + i];
+          g[a][0] = -gs * (sx.hi + sx.lo);
+          g[a][1] = -gs * (sy.hi + sy.lo);
+          g[a][2] = -gs * (sz.hi + sz.lo);
+        } else {
+          g[a][0] = (XG)0; g[a][1] = (XG)0; g[a][2] = (XG)0;
+        }
+        if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+      }
+      E = ff_scale(team_sum_ff<T>(tm, e), p.k.e4_f);
+      if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+      return;
+    }
+    }
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int i = tm.rank + a * T;

@@ -25,11 +25,19 @@ __host__ __device__ constexpr int cta_threads_for(int T) { return T < 128 ? 128 
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// Half-pair buffers are used for clusters of up to kHalfMaxN atoms.
+// Half-pair buffers (24 bytes per pair) are used for clusters of up to
+// kHalfMaxN atoms; teams for more than kTileMinN atoms hold the
+// double-float tile accumulators (24 bytes per atom) in the same slot; in
+// between, double-float evaluations are one-sided (measured: with 3 to 8
+// atom blocks a tile round leaves warps idle).
 constexpr int kHalfMaxN = 64;
+constexpr int kTileMinN = 256;
 
 __host__ __device__ constexpr size_t half_bytes(int max_n, bool half) {
-  return (half && max_n <= kHalfMaxN) ? align16((size_t)24 * (max_n * (max_n - 1) / 2)) : 0;
+  return !half ? 0
+         : max_n <= kHalfMaxN ? align16((size_t)24 * (max_n * (max_n - 1) / 2))
+         : max_n > kTileMinN  ? align16((size_t)24 * max_n)
+                              : 0;
 }
 
 // per-team shared bytes: positions (32-byte records; the FP32 phase uses the
