@@ -313,6 +313,25 @@ def test_minimise_cube_starts(lj, ctx, prec, n_atoms, side, cfg):
         assert diff <= 3 * se
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_lj38_truncated_octahedron(lj, ctx, prec):
+    """The structure the paper names as LJ38's global minimum (fcc truncated
+    octahedron, O_h): GPU minimisation from it reaches the oracle's minimum
+    energy and keeps the O_h symmetry."""
+    from tests.test_oracle_pins import oh_operations, truncated_octahedron_38
+    x0 = truncated_octahedron_38().reshape(1, -1)
+    xo, eo, so, _, _ = O.lbfgs_batch(x0, 1, uniform_n=38)
+    xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, uniform_n=38, prec=prec)
+    assert sg[0] == O.CONVERGED and so[0] == O.CONVERGED
+    tol = FP64_REL_E * abs(eo[0]) if prec == 0 else MIX_ABS_FINAL
+    assert abs(eg[0] - eo[0]) <= tol
+    p = xg.reshape(38, 3)
+    p = p - p.mean(0)
+    for m in oh_operations():
+        d = np.linalg.norm((p @ m.T)[:, None, :] - p[None, :, :], axis=2).min(1)
+        assert d.max() < 1e-5
+
+
 # large clusters: perturbed fcc fragments (0.1 sigma jitter), m = 20; the GPU
 # minimises a batch, the oracle the first candidates of it
 LARGE_CASES = [(500, 12, 2), (1000, 6, 1)]
