@@ -272,8 +272,10 @@ __device__ __forceinline__ void stage_f32x2(PosF2* pos, int n, int i, float x, f
 // `pos`: b = sum_j c_ij (x_j - x_i) with c = s2 s6 (2 s6 - 1), s2 = sigma^2
 // / r^2 (SIG: sigma != 1, sig2 = sigma^2), and e += sum_j s6 (s6 - 1), the
 // self term excluded.  Energy: per lane, blocks of 4 terms summed in FP32,
-// the two lanes' block sums added and folded into the float-float `e`.
-template <bool SIG>
+// the two lanes' block sums added and folded into the float-float `e`
+// (FF), or summed in plain FP32 into e.hi (!FF: ~8 ulps of the row, below the
+// pair terms' own error; used where the energy is only reported).
+template <bool SIG, bool FF = true>
 __device__ __forceinline__ void pair_row_f32x2(int n, int i, float px, float py, float pz,
                                                const PosF2* __restrict__ pos, float sig2,
                                                float& bx, float& by, float& bz, ff& e) {
@@ -306,12 +308,14 @@ __device__ __forceinline__ void pair_row_f32x2(int n, int i, float px, float py,
     float2 eb = f2(0.f);
 #pragma unroll
     for (int u = 0; u < 4; ++u) term(m + u, eb);
-    e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
+    if constexpr (FF) e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
+    else e.hi = __fadd_rn(e.hi, __fadd_rn(eb.x, eb.y));
   }
   if (m < M) {
     float2 eb = f2(0.f);
     for (; m < M; ++m) term(m, eb);
-    e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
+    if constexpr (FF) e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
+    else e.hi = __fadd_rn(e.hi, __fadd_rn(eb.x, eb.y));
   }
   bx = __fadd_rn(ax.x, ax.y);
   by = __fadd_rn(ay.x, ay.y);

@@ -81,9 +81,8 @@ constexpr int kFlatThreads = 512;
 // pair-packed records (double-buffered, so one barrier orders both the
 // staging and the reuse of the other buffer), the next tile's coordinates are
 // already loading while this tile computes, each thread sums the packed FP32
-// row of its own atom (one-sided, no atomics, float-float energy), and the
-// per-atom energies are combined in a fixed order: rounded to FP32 (0.5 ulp
-// of a row, far below the pair terms' own error) and summed by a segmented
+// row of its own atom (one-sided, no atomics, FP32 block sums), and the
+// per-atom energies are combined in a fixed order: summed by a segmented
 // shuffle tree within each warp, then the (at most S) warp segments of a
 // candidate are added in FP64.  That FP64 step is done by the first C
 // threads together (one warp for N >= 16), because an FP64 instruction costs
@@ -142,9 +141,9 @@ __global__ void __launch_bounds__(kFlatThreads) eval_flat_f32_kernel(ljh::EvalAr
     if (live) {
       float bx, by, bz;
       if (unit)
-        pair_row_f32x2<false>(n, i, px, py, pz, pos2, 1.f, bx, by, bz, e);
+        pair_row_f32x2<false, false>(n, i, px, py, pz, pos2, 1.f, bx, by, bz, e);
       else
-        pair_row_f32x2<true>(n, i, px, py, pz, pos2, a.k.sig2_f, bx, by, bz, e);
+        pair_row_f32x2<true, false>(n, i, px, py, pz, pos2, a.k.sig2_f, bx, by, bz, e);
       if (gout) {
         const long long q = 3 * (c * n + i);
         gout[q] = (IO)(gs * bx);
