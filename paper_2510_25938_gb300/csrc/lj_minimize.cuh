@@ -423,8 +423,7 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 // g.d back: two team barriers per direction instead of 2 cnt + 1.  Same
 // operations and order as the team version, per warp-sized partial sums.
 // ---------------------------------------------------------------------------
-template <int V0>
-__device__ __forceinline__ float warp_sum(float v) {
+__device__ __forceinline__ float warp_sum(float v) {   // xor butterfly: every lane gets the sum
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
@@ -468,7 +467,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 #pragma unroll
           for (int c = 0; c < 3; ++c)
             part += Sh[hidx<T, A>(sl, a, c, lane + 32 * w)] * q[w][a][c];
-      const float al = rho[sl] * warp_sum<0>(part);
+      const float al = rho[sl] * warp_sum(part);
       alpha[t] = al;
 #pragma unroll
       for (int w = 0; w < W; ++w)
@@ -494,7 +493,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 #pragma unroll
           for (int c = 0; c < 3; ++c)
             part += Yh[hidx<T, A>(sl, a, c, lane + 32 * w)] * q[w][a][c];
-      const float coef = alpha[t] - rho[sl] * warp_sum<0>(part);
+      const float coef = alpha[t] - rho[sl] * warp_sum(part);
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -512,7 +511,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
           xb[(a * 3 + c) * T + lane + 32 * w] = -q[w][a][c];
           part += gl[w][a][c] * -q[w][a][c];
         }
-    const float dphi = warp_sum<0>(part);
+    const float dphi = warp_sum(part);
     if (lane == 0) xb[A * 3 * T] = dphi;
   }
   tm.sync();
