@@ -182,6 +182,37 @@ __device__ __forceinline__ ff team_sum_ff(const Team<T>& tm, ff v) {
   return v;
 }
 
+// team_sum_ff of e and team_sum of x in one pass (one cross-warp exchange):
+// each value gets exactly the operations, in the order, of its own reduction
+template <int T>
+__device__ __forceinline__ void team_sum_ff_f(const Team<T>& tm, ff& e, float& x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ff w{shfl_xor(e.hi, o), shfl_xor(e.lo, o)};
+    e = ff_add(e, w);
+    x += shfl_xor(x, o);
+  }
+  if constexpr (T > 32) {
+    constexpr int NW = T / 32;
+    float* buf = reinterpret_cast<float*>(tm.scratch());
+    if ((tm.rank & 31) == 0) {
+      buf[3 * (tm.rank >> 5)] = e.hi;
+      buf[3 * (tm.rank >> 5) + 1] = e.lo;
+      buf[3 * (tm.rank >> 5) + 2] = x;
+    }
+    tm.sync();
+    ff s{buf[0], buf[1]};
+    float t = buf[2];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) {
+      s = ff_add(s, ff{buf[3 * w], buf[3 * w + 1]});
+      t += buf[3 * w + 2];
+    }
+    e = s;
+    x = t;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from the published round
 // function and key schedule, and the 53-bit uniform built from two words.

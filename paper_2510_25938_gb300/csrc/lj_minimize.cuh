@@ -343,6 +343,14 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
       }
       if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
     }
+    if constexpr (std::is_same<V, float>::value) {
+      if (d) {                  // energy and g.d in one team reduction
+        team_sum_ff_f<T>(tm, e, dp);
+        E = ff_scale(e, p.k.e2_f);
+        dphi = (S)dp;
+        return;
+      }
+    }
     ff et = team_sum_ff<T>(tm, e);
     E = ff_scale(et, p.k.e2_f);
   } else {
@@ -458,23 +466,35 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
           q[w][a][c] = gl[w][a][c];
         }
     for (int t = cnt - 1; t >= 0; --t) {
+      // both vectors of the pair are loaded before the reduction, so that
+      // their latency is not paid again after it
       const int sl = slot_of(t);
+      float sv[W][A][3], yv[W][A][3];
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sv[w][a][c] = Sh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+            yv[w][a][c] = Yh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+          }
+      const float r = rho[sl];
       float part = 0.f;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            part += Sh[hidx<T, A>(sl, a, c, lane + 32 * w)] * q[w][a][c];
-      const float al = rho[sl] * warp_sum(part);
+          for (int c = 0; c < 3; ++c) part += sv[w][a][c] * q[w][a][c];
+      const float al = r * warp_sum(part);
       alpha[t] = al;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) q[w][a][c] -= al * Yh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+          for (int c = 0; c < 3; ++c) q[w][a][c] -= al * yv[w][a][c];
     }
     const float gam = gmv[slot_of(cnt - 1)];
 #pragma unroll
@@ -485,21 +505,32 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
         for (int c = 0; c < 3; ++c) q[w][a][c] *= gam;
     for (int t = 0; t < cnt; ++t) {
       const int sl = slot_of(t);
+      float sv[W][A][3], yv[W][A][3];
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sv[w][a][c] = Sh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+            yv[w][a][c] = Yh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+          }
+      const float r = rho[sl];
+      const float at = alpha[t];
       float part = 0.f;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            part += Yh[hidx<T, A>(sl, a, c, lane + 32 * w)] * q[w][a][c];
-      const float coef = alpha[t] - rho[sl] * warp_sum(part);
+          for (int c = 0; c < 3; ++c) part += yv[w][a][c] * q[w][a][c];
+      const float coef = at - r * warp_sum(part);
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) q[w][a][c] += coef * Sh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+          for (int c = 0; c < 3; ++c) q[w][a][c] += coef * sv[w][a][c];
     }
     float part = 0.f;
 #pragma unroll
