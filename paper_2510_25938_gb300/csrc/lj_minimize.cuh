@@ -163,6 +163,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   tm.sync();
   V dp = (V)0;
   if constexpr (PM == 1 || std::is_same<X, double>::value) {
+    ff e_df{0.f, 0.f};          // PM == 1: this thread's pair energies
     if (hbuf != nullptr && !p.tiled) {
       // ---- half-pair evaluation ---------------------------------------------
       // pair phase: thread `rank` takes pairs rank, rank + T, ...; two pairs
@@ -216,9 +217,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           gsum[q3] = -gs * (sum.hi + sum.lo);
         }
         tm.sync();
-        // float-float team sum (FP32 pipes): its ~2^-47 relative error is far
-        // below the double-float handover resolution
-        E = ff_scale(team_sum_ff<T>(tm, e), p.k.e4_f);
+        e_df = e;               // reduced below, together with g.d
       } else {
         const PosD* pos = static_cast<const PosD*>(posv);
         double* vb = static_cast<double*>(hbuf);
@@ -272,6 +271,19 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
         }
         if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
       }
+      if constexpr (PM == 1) {
+        // float-float team sum (FP32 pipes): its ~2^-47 relative error is far
+        // below the double-float handover resolution; g.d in the same pass
+        if constexpr (std::is_same<V, float>::value) {
+          if (d) {
+            team_sum_ff_f<T>(tm, e_df, dp);
+            E = ff_scale(e_df, p.k.e4_f);
+            dphi = (S)dp;
+            return;
+          }
+        }
+        E = ff_scale(team_sum_ff<T>(tm, e_df), p.k.e4_f);
+      }
       if (d) dphi = (S)team_sum1<T, V>(tm, dp);
       return;
     }
@@ -298,6 +310,14 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           g[a][0] = (XG)0; g[a][1] = (XG)0; g[a][2] = (XG)0;
         }
         if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+      }
+      if constexpr (std::is_same<V, float>::value) {
+        if (d) {
+          team_sum_ff_f<T>(tm, e, dp);
+          E = ff_scale(e, p.k.e4_f);
+          dphi = (S)dp;
+          return;
+        }
       }
       E = ff_scale(team_sum_ff<T>(tm, e), p.k.e4_f);
       if (d) dphi = (S)team_sum1<T, V>(tm, dp);
@@ -880,7 +900,16 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         pr[0] += sv[a][c] * yv[a][c];
         pr[1] += yv[a][c] * yv[a][c];
       }
-    team_sum<T, 2, V>(tm, pr);
+    // stopping-test values of the new point (||g||_inf, deadline), reduced
+    // in the same pass as the curvature pair's s.y and y.y
+    XG mv[2];
+    mv[0] = (XG)0;
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mv[0] = fmax(mv[0], abs_nan_inf(gt[a][c]));
+    mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (XG)1 : (XG)0;
+    team_sum2_max2<T, V, XG>(tm, pr, mv);
     if (pr[0] > eps_mach<V>() * pr[1]) {
       int slot;
       if (cnt < m) {
@@ -911,15 +940,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
     f = ft;
     ++iters;
     ++phase_iters;
-    // ---- stopping tests ----------------------------------------------------
-    XG mv[2];
-    mv[0] = (XG)0;
-#pragma unroll
-    for (int a = 0; a < A; ++a)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) mv[0] = fmax(mv[0], abs_nan_inf(g[a][c]));
-    mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (XG)1 : (XG)0;
-    team_max<T, 2, XG>(tm, mv);
+    // ---- stopping tests (values reduced above) -----------------------------
     if (mv[0] < stop_gtol) return MODE == 1 ? PH_SWITCH : PH_CONVERGED;
     if (mv[1] > (XG)0) return PH_TIMEOUT;
     if constexpr (MODE == 1) {
