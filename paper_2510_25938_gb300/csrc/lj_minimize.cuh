@@ -636,8 +636,8 @@ __device__ __forceinline__ float table_two_loop(const Team<T>& tm, int m, int cn
       yn[a][cc] = Yh[hidx<T, A>(sl0, a, cc, tm.rank)];
     }
   // two passes of 32 values (a_k, b_k; then s_k.y_new, y_k.y_new), each
-  // reduce-scattered over the warp: the level of offset o keeps the half
-  // selected by lane bit o, so lane l ends with the total of value l
+  // reduce-scattered over the warp: lane l ends with value rev5(l) of a pass
+  const int rl = (int)(__brev((unsigned)lane) >> 27);
 #pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
     float pv[2 * MC];
@@ -663,7 +663,7 @@ __device__ __forceinline__ float table_two_loop(const Team<T>& tm, int m, int cn
     rs_level<8>(pv, (lane & 4) != 0, 4);
     rs_level<4>(pv, (lane & 2) != 0, 2);
     rs_level<2>(pv, (lane & 1) != 0, 1);
-    scr[wid * 64 + pass * 32 + lane] = pv[0];
+    scr[wid * 64 + pass * 32 + rl] = pv[0];
   }
   tm.sync();
 
