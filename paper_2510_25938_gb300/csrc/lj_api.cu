@@ -58,22 +58,18 @@ lj_status cuda_fail(lj_ctx* ctx, cudaError_t e, const char* where) {
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // history bytes per team slot for a given atom bound (largest team variant
-// of that bound; FP64 history, or float history and its inner-product
-// tables, whichever is larger) -- used only to size reservations
+// of that bound, FP64 history) -- used only to size reservations
 size_t slot_bytes_bound(int max_n, int m) {
   int T = 32, A = 1;
   if (max_n <= 64) {               // any team choice: T * A <= 128
-    T = 128;
-  } else {
-    A = 2;
-    if (max_n > 64) T = 64;
-    if (max_n > 128) T = 128;
-    if (max_n > 256) T = 256;
-    if (max_n > 512) T = 512;
+    return (2 * (size_t)m * 128 * 3 * sizeof(double) + 15) & ~size_t(15);
   }
-  const size_t vals = 2 * (size_t)m * A * 3 * T;
-  auto a16 = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return std::max(a16(vals * sizeof(double)), a16(vals * sizeof(float)) + ljh::table_bytes(T, m));
+  if (max_n > 32) A = 2;
+  if (max_n > 64) T = 64;
+  if (max_n > 128) T = 128;
+  if (max_n > 256) T = 256;
+  if (max_n > 512) T = 512;
+  return (2 * (size_t)m * A * 3 * T * sizeof(double) + 15) & ~size_t(15);
 }
 
 lj_status ensure_ws(lj_ctx* ctx, size_t bytes) {

@@ -223,8 +223,7 @@ __global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
 
 template <int T, int A, bool MIXED>
 cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out) {
-  out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double))) +
-                    (MIXED ? ljh::table_bytes(T, m) : 0);
+  out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
   out->team = T;
   if (K <= LJ_MAX_K) {                // one cluster of K CTAs per walker
     const bool on_chip = bhc_head_bytes<T>(n_atoms) +

@@ -11,20 +11,6 @@ namespace ljd { struct MinParams; }
 
 namespace ljh {
 
-// Inner-product tables of the float L-BFGS history, kept after it in the same
-// slot for teams of up to 128 threads and history lengths up to kTableM:
-// s_i.y_j and y_i.y_j by slot (two m x (m | 1) tables; the odd row stride
-// keeps a warp's per-lane rows in distinct banks) and a reduction scratch of
-// 64 floats per warp.
-constexpr int kTableM = 16;
-__host__ __device__ constexpr int table_stride(int m) { return m | 1; }
-__host__ __device__ constexpr size_t table_bytes(int T, int m) {
-  return (T <= 128 && m <= kTableM)
-             ? ((((size_t)2 * m * table_stride(m) + 64 * (size_t)(T / 32)) * sizeof(float) + 15) &
-                ~size_t(15))
-             : 0;
-}
-
 struct MinParamsH {     // mirror of ljd::MinParams (plain data)
   int m, max_iter, max_ls;
   double gtol, c1, c2, alpha_max, switch_gtol;

@@ -133,8 +133,7 @@ template <int T, int A, bool MIXED>
 cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out) {
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
-  const size_t hist_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double))) +
-                            (MIXED ? ljh::table_bytes(T, m) : 0);
+  const size_t hist_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
   const bool on_chip = TPC * team_smem_bytes<T>(max_n, true, hist_bytes) <= kSmemBudget;
   const size_t smem = TPC * team_smem_bytes<T>(max_n, true, on_chip ? hist_bytes : 0);
   auto k = lbfgs_kernel<T, A, MIXED>;

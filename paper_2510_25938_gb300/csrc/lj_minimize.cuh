@@ -36,7 +36,6 @@
 
 #include "lj_device.cuh"
 #include "lj_consts.h"
-#include "lj_internal.h"
 #include "../../include/lj_bh.h"
 
 namespace ljd {
@@ -575,173 +574,6 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 }
 
 // ---------------------------------------------------------------------------
-// Two-loop recursion on inner-product tables (float history, teams of up to
-// 128 threads, m <= kTableM).  With a_k = s_k.g, b_k = y_k.g and the tables
-// R(i, k) = s_i.y_k (pair i older than k) and Y(i, k) = y_i.y_k, the
-// recursion of Algorithm 7.4 of Nocedal & Wright needs no further vector
-// work until the final combination:
-//   alpha_k = rho_k (a_k - sum_{j newer than k} alpha_j R(k, j))   newest first
-//   v_k     = gamma (b_k - sum_j alpha_j Y(k, j))
-//   beta_k  = rho_k v_k,  v_i += (alpha_k - beta_k) R(k, i)           oldest first,
-//                                                         for i newer than k
-//   d       = -(gamma g - sum_k gamma alpha_k y_k + sum_k (alpha_k - beta_k) s_k)
-// (the same quantities as the vector recursion; its inner products of the
-// updated vectors are expanded into the tables).  Of the tables only the
-// newest pair's column changes between directions, so each direction reduces
-// 4 x 16 values in one pass -- a_k, b_k, s_k.y_new, y_k.y_new -- instead of
-// running 2 cnt dependent team reductions; the scalar recurrences then run
-// lane-parallel in every warp (lane k owns the pair of age k; age 0 is the
-// newest) with one shuffle per step.  The newest column is recomputed on
-// every call, so a step whose pair was not stored (curvature test) or a
-// history reset needs no bookkeeping.
-// ---------------------------------------------------------------------------
-template <int C>
-__device__ __forceinline__ void rs_level(float* v, bool up, int o) {
-  // reduce-scatter step: keep one half of v, add the partner's copy of it
-#pragma unroll
-  for (int i = 0; i < C / 2; ++i) {
-    const float lo = v[i], hi = v[i + C / 2];
-    v[i] = (up ? hi : lo) + __shfl_xor_sync(kFull, up ? lo : hi, o);
-  }
-}
-
-template <int T, int A, typename XG>
-__device__ __forceinline__ float table_two_loop(const Team<T>& tm, int m, int cnt, int head,
-                                                const float* __restrict__ Sh,
-                                                const float* __restrict__ Yh,
-                                                float* __restrict__ tab,
-                                                const float (&rho)[LJ_MAX_M],
-                                                const float (&gmv)[LJ_MAX_M],
-                                                const XG (&g)[A][3], float (&d)[A][3]) {
-  constexpr int MC = ljh::kTableM;      // ages per value group
-  constexpr int W = T / 32;
-  static_assert(2 * MC == 32, "32 values per reduction pass");
-  const int ms = ljh::table_stride(m);
-  float* Rt = tab;                      // Rt[slot_i * ms + slot_k] = s_i . y_k
-  float* Yt = tab + m * ms;             // Yt[slot_i * ms + slot_k] = y_i . y_k
-  float* scr = tab + 2 * m * ms;        // 64 floats per warp
-  const int c = cnt;
-  const int lane = tm.rank & 31;
-  const int wid = tm.rank >> 5;
-  auto slot_age = [&](int k) { const int s = head + c - 1 - k; return s >= m ? s - m : s; };
-  const int sl0 = slot_age(0);
-
-  // ---- per-thread partial inner products of every stored pair -------------
-  float gv[A][3], yn[A][3];
-#pragma unroll
-  for (int a = 0; a < A; ++a)
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      gv[a][cc] = (float)g[a][cc];
-      yn[a][cc] = Yh[hidx<T, A>(sl0, a, cc, tm.rank)];
-    }
-  // two passes of 32 values (a_k, b_k; then s_k.y_new, y_k.y_new), each
-  // reduce-scattered over the warp: lane l ends with value rev5(l) of a pass
-  const int rl = (int)(__brev((unsigned)lane) >> 27);
-#pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-    float pv[2 * MC];
-#pragma unroll
-    for (int k = 0; k < MC; ++k) {
-      float p0 = 0.f, p1 = 0.f;
-      if (k < c) {
-        const int sk = slot_age(k);
-#pragma unroll
-        for (int a = 0; a < A; ++a)
-#pragma unroll
-          for (int cc = 0; cc < 3; ++cc) {
-            const float w = pass == 0 ? gv[a][cc] : yn[a][cc];
-            p0 += Sh[hidx<T, A>(sk, a, cc, tm.rank)] * w;
-            p1 += Yh[hidx<T, A>(sk, a, cc, tm.rank)] * w;
-          }
-      }
-      pv[k] = p0;
-      pv[MC + k] = p1;
-    }
-    rs_level<32>(pv, (lane & 16) != 0, 16);
-    rs_level<16>(pv, (lane & 8) != 0, 8);
-    rs_level<8>(pv, (lane & 4) != 0, 4);
-    rs_level<4>(pv, (lane & 2) != 0, 2);
-    rs_level<2>(pv, (lane & 1) != 0, 1);
-    scr[wid * 64 + pass * 32 + rl] = pv[0];
-  }
-  tm.sync();
-
-  // ---- the pair of age `lane` (lanes < c): its four sums --------------------
-  const bool own = lane < c;
-  const int si = own ? slot_age(lane) : 0;
-  float ai = 0.f, bi = 0.f, ri = 0.f, yi = 0.f;
-  if (own) {
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      ai += scr[w * 64 + lane];
-      bi += scr[w * 64 + MC + lane];
-      ri += scr[w * 64 + 2 * MC + lane];
-      yi += scr[w * 64 + 3 * MC + lane];
-    }
-  }
-  // the newest column, kept for later calls (this call reads it from ri, yi:
-  // no entry written here is read before the next call)
-  if (wid == 0 && own) {
-    Rt[si * ms + sl0] = ri;
-    Yt[si * ms + sl0] = yi;
-    Yt[sl0 * ms + si] = yi;
-  }
-  const float rh = own ? rho[si] : 0.f;
-  const float gam = gmv[sl0];
-
-  // ---- first loop, newest first: alpha_k ------------------------------------
-  float u = ai, al = 0.f;
-  for (int k = 0; k < c; ++k) {
-    const float ak = __shfl_sync(kFull, rh * u, k);
-    if (lane == k) al = ak;
-    if (own && lane > k) u -= ak * (k == 0 ? ri : Rt[si * ms + slot_age(k)]);
-  }
-  // ---- v_i = gamma (b_i - sum_j alpha_j Y(i, j)) ------------------------------
-  float v = bi;
-  for (int j = 0; j < c; ++j) {
-    const float aj = __shfl_sync(kFull, al, j);
-    const float yj = __shfl_sync(kFull, yi, j);       // y_j . y_new (lane 0's row)
-    const float yij = lane == 0 ? yj : (j == 0 ? yi : (own ? Yt[si * ms + slot_age(j)] : 0.f));
-    v -= aj * yij;
-  }
-  v *= gam;
-  // ---- second loop, oldest first: alpha_k - beta_k ----------------------------
-  float cf = 0.f;
-  for (int k = c - 1; k >= 0; --k) {
-    const float ck = __shfl_sync(kFull, al - rh * v, k);
-    const float rk = __shfl_sync(kFull, ri, k);       // s_k . y_new (lane 0's entry)
-    if (lane == k) cf = ck;
-    if (lane < k) v += ck * (lane == 0 ? rk : Rt[slot_age(k) * ms + si]);
-  }
-  // ---- d = -(gamma g - sum gamma alpha_k y_k + sum (alpha_k - beta_k) s_k) ----
-  float q[A][3];
-#pragma unroll
-  for (int a = 0; a < A; ++a)
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) q[a][cc] = -gam * gv[a][cc];
-  for (int k = 0; k < c; ++k) {
-    const float gak = gam * __shfl_sync(kFull, al, k);
-    const float ck = __shfl_sync(kFull, cf, k);
-    const int sk = slot_age(k);
-#pragma unroll
-    for (int a = 0; a < A; ++a)
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc)
-        q[a][cc] += gak * Yh[hidx<T, A>(sk, a, cc, tm.rank)] - ck * Sh[hidx<T, A>(sk, a, cc, tm.rank)];
-  }
-  float part = 0.f;
-#pragma unroll
-  for (int a = 0; a < A; ++a)
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      d[a][cc] = q[a][cc];
-      part += gv[a][cc] * q[a][cc];
-    }
-  return team_sum1<T, float>(tm, part);
-}
-
-// ---------------------------------------------------------------------------
 // One L-BFGS phase: iterate from (x, g, f) until a stop condition.
 // X: coordinates/gradient precision, V: direction/history precision,
 // PM: pair arithmetic (0 native X, 1 double-float).
@@ -786,16 +618,8 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
     long long tc = clock64();
     S dphi0 = (S)1;
     bool led = false;
-    if constexpr (std::is_same<V, float>::value && T <= 128) {
-      if (cnt > 0 && m <= ljh::kTableM) {
-        dphi0 = (S)table_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh,
-                                            Yh + (size_t)m * A * 3 * T, rho, gmv, g, d);
-        vec += (long long)cnt * 3 * n;
-        led = true;
-      }
-    }
     if constexpr (std::is_same<V, float>::value && T > 32 && T <= 128) {
-      if (cnt > 0 && !led && 12 * A * T + 4 <= 32 * n) {
+      if (cnt > 0 && 12 * A * T + 4 <= 32 * n) {
         dphi0 = (S)lead_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh, rho, gmv, g,
                                            static_cast<float*>(pos), d);
         vec += (long long)cnt * 3 * n;
