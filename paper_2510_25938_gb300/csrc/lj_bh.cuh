@@ -50,8 +50,13 @@ __host__ __device__ constexpr size_t bhc_head_bytes(int n_atoms) {
   return align16(sizeof(BhShared)) + 16 + 3 * align16((size_t)3 * n_atoms * sizeof(double));
 }
 
+// Teams of up to 64 threads ask for 3 CTAs per SM, which leaves ptxas the
+// full 255 registers (no spills); its default stopped at 168 with spills.
+// Measured on LJ38, 64 walkers x K = 8: 23.9 against 25.9 ms per 10-step
+// launch.  At 255 registers 4 CTAs of 64 threads fit on an SM (608 on 152
+// SMs, more than the 512 CTAs of that workload).
 template <int T, int A, bool MIXED>
-__global__ void __launch_bounds__(T) bh_cluster_kernel(ljh::BhArgs a) {
+__global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int n = a.n_atoms;
