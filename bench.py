@@ -53,7 +53,7 @@ FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of G
 # dram__bytes_read.sum + dram__bytes_write.sum of one bh_cluster_kernel launch of this
 # workload (ncu capture summarised in profiles/bh_cluster_kernel_lj38_64x8.md); set to
 # None whenever the kernel changes until it is captured again
-BH_DRAM_BYTES_PER_LAUNCH = 384512 + 0
+BH_DRAM_BYTES_PER_LAUNCH = None
 
 
 def parse():

@@ -182,43 +182,43 @@ __device__ __forceinline__ ff team_sum_ff(const Team<T>& tm, ff v) {
   return v;
 }
 
-// team_sum of s[0..1] and team_max of m[0..1] (inputs >= 0, non-finite as
-// +inf) in one pass, one cross-warp exchange; each value gets the operations
-// of its own reduction in the same order
-template <int T, typename V, typename M>
-__device__ __forceinline__ void team_sum2_max2(const Team<T>& tm, V (&s)[2], M (&m)[2]) {
+// team_sum of s[0..NS-1] and team_max of m[0..1] (inputs >= 0, non-finite
+// as +inf) in one pass, one cross-warp exchange; each value gets the
+// operations of its own reduction in the same order
+template <int T, typename V, typename M, int NS>
+__device__ __forceinline__ void team_sums_max2(const Team<T>& tm, V (&s)[NS], M (&m)[2]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      s[k] += shfl_xor(s[k], o);
-      m[k] = fmax(m[k], shfl_xor(m[k], o));
-    }
+    for (int k = 0; k < NS; ++k) s[k] += shfl_xor(s[k], o);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) m[k] = fmax(m[k], shfl_xor(m[k], o));
   }
   if constexpr (T > 32) {
     constexpr int NW = T / 32;
-    static_assert(2 * sizeof(V) + 2 * sizeof(M) <= 8 * sizeof(double), "reduction scratch");
+    static_assert(NS * sizeof(V) + 2 * sizeof(M) <= 8 * sizeof(double), "reduction scratch");
     unsigned char* raw = reinterpret_cast<unsigned char*>(tm.scratch());
     V* bs = reinterpret_cast<V*>(raw);
-    M* bm = reinterpret_cast<M*>(raw + 2 * NW * sizeof(V));
+    M* bm = reinterpret_cast<M*>(raw + ((NS * NW * sizeof(V) + sizeof(M) - 1) / sizeof(M)) * sizeof(M));
     if ((tm.rank & 31) == 0) {
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        bs[(tm.rank >> 5) * 2 + k] = s[k];
-        bm[(tm.rank >> 5) * 2 + k] = m[k];
-      }
+      for (int k = 0; k < NS; ++k) bs[(tm.rank >> 5) * NS + k] = s[k];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) bm[(tm.rank >> 5) * 2 + k] = m[k];
     }
     tm.sync();
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < NS; ++k) {
       V a = bs[k];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) a += bs[w * NS + k];
+      s[k] = a;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
       M b = bm[k];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        a += bs[w * 2 + k];
-        b = fmax(b, bm[w * 2 + k]);
-      }
-      s[k] = a;
+      for (int w = 1; w < NW; ++w) b = fmax(b, bm[w * 2 + k]);
       m[k] = b;
     }
   }

@@ -448,13 +448,31 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 // position buffer, 12 A T + 4 bytes), warp 0 runs the recursion over all T
 // ranks' entries (lane l covers ranks l, l + 32, ...: the history is
 // addressable by rank) with shuffle-only reductions, and stages d and
-// g.d back: two team barriers per direction instead of 2 cnt + 1.  Same
-// operations and order as the team version, per warp-sized partial sums.
+// g.d back: two team barriers per direction instead of 2 cnt + 1.
+//
+// Pairs are taken two at a time, so that one two-value reduction serves two
+// steps of each loop.  With q the vector before pair t (first loop, newest
+// first) the next pair's product follows from this one's:
+//   s_{t-1}.(q - alpha_t y_t) = s_{t-1}.q - alpha_t (s_{t-1}.y_t),
+// and in the second loop (oldest first), with r before pair t,
+//   y_{t+1}.(r + c_t s_t) = y_{t+1}.r + c_t (s_t.y_{t+1}),  c_t = alpha_t - beta_t.
+// s_{t-1}.y_t -- the previous pair's s against this pair's y -- is reduced
+// when pair t is stored (`sup`).  The same quantities as the one-at-a-time
+// recursion (Algorithm 7.4 of Nocedal & Wright), half as many dependent
+// reductions.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v) {   // xor butterfly: every lane gets the sum
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+__device__ __forceinline__ void warp_sum2(float& v0, float& v1) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(kFull, v0, o);
+    v1 += __shfl_xor_sync(kFull, v1, o);
+  }
 }
 
 template <int T, int A, typename XG>
@@ -463,6 +481,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
                                                const float* __restrict__ Yh,
                                                const float (&rho)[LJ_MAX_M],
                                                const float (&gmv)[LJ_MAX_M],
+                                               const float (&sup)[LJ_MAX_M],
                                                const XG (&g)[A][3], float* xb,
                                                float (&d)[A][3]) {
   constexpr int W = T / 32;
@@ -485,36 +504,75 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
           gl[w][a][c] = xb[(a * 3 + c) * T + lane + 32 * w];
           q[w][a][c] = gl[w][a][c];
         }
-    for (int t = cnt - 1; t >= 0; --t) {
-      // both vectors of the pair are loaded before the reduction, so that
-      // their latency is not paid again after it
-      const int sl = slot_of(t);
-      float sv[W][A][3], yv[W][A][3];
+    // ---- first loop, newest first --------------------------------------------
+    int t = cnt - 1;
+    for (; t >= 1; t -= 2) {
+      const int s0 = slot_of(t), s1 = slot_of(t - 1);
+      float sv0[W][A][3], yv0[W][A][3], sv1[W][A][3], yv1[W][A][3];
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            sv[w][a][c] = Sh[hidx<T, A>(sl, a, c, lane + 32 * w)];
-            yv[w][a][c] = Yh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+            sv0[w][a][c] = Sh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+            yv0[w][a][c] = Yh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+            sv1[w][a][c] = Sh[hidx<T, A>(s1, a, c, lane + 32 * w)];
+            yv1[w][a][c] = Yh[hidx<T, A>(s1, a, c, lane + 32 * w)];
           }
-      const float r = rho[sl];
+      const float r0 = rho[s0], r1 = rho[s1], u01 = sup[s0];
+      float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            p0 += sv0[w][a][c] * q[w][a][c];
+            p1 += sv1[w][a][c] * q[w][a][c];
+          }
+      warp_sum2(p0, p1);
+      const float a0 = r0 * p0;
+      const float a1 = r1 * (p1 - a0 * u01);
+      alpha[t] = a0;
+      alpha[t - 1] = a1;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            q[w][a][c] -= a0 * yv0[w][a][c];
+            q[w][a][c] -= a1 * yv1[w][a][c];
+          }
+    }
+    if (t == 0) {
+      const int s0 = slot_of(0);
+      float sv0[W][A][3], yv0[W][A][3];
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sv0[w][a][c] = Sh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+            yv0[w][a][c] = Yh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+          }
       float part = 0.f;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) part += sv[w][a][c] * q[w][a][c];
-      const float al = r * warp_sum(part);
-      alpha[t] = al;
+          for (int c = 0; c < 3; ++c) part += sv0[w][a][c] * q[w][a][c];
+      const float a0 = rho[s0] * warp_sum(part);
+      alpha[0] = a0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) q[w][a][c] -= al * yv[w][a][c];
+          for (int c = 0; c < 3; ++c) q[w][a][c] -= a0 * yv0[w][a][c];
     }
     const float gam = gmv[slot_of(cnt - 1)];
 #pragma unroll
@@ -523,34 +581,73 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
       for (int a = 0; a < A; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) q[w][a][c] *= gam;
-    for (int t = 0; t < cnt; ++t) {
-      const int sl = slot_of(t);
-      float sv[W][A][3], yv[W][A][3];
+    // ---- second loop, oldest first ---------------------------------------------
+    t = 0;
+    for (; t + 1 < cnt; t += 2) {
+      const int s0 = slot_of(t), s1 = slot_of(t + 1);
+      float sv0[W][A][3], yv0[W][A][3], sv1[W][A][3], yv1[W][A][3];
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            sv[w][a][c] = Sh[hidx<T, A>(sl, a, c, lane + 32 * w)];
-            yv[w][a][c] = Yh[hidx<T, A>(sl, a, c, lane + 32 * w)];
+            sv0[w][a][c] = Sh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+            yv0[w][a][c] = Yh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+            sv1[w][a][c] = Sh[hidx<T, A>(s1, a, c, lane + 32 * w)];
+            yv1[w][a][c] = Yh[hidx<T, A>(s1, a, c, lane + 32 * w)];
           }
-      const float r = rho[sl];
-      const float at = alpha[t];
+      const float r0 = rho[s0], r1 = rho[s1], u01 = sup[s1];
+      const float al0 = alpha[t], al1 = alpha[t + 1];
+      float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            p0 += yv0[w][a][c] * q[w][a][c];
+            p1 += yv1[w][a][c] * q[w][a][c];
+          }
+      warp_sum2(p0, p1);
+      const float c0 = al0 - r0 * p0;
+      const float c1 = al1 - r1 * (p1 + c0 * u01);
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            q[w][a][c] += c0 * sv0[w][a][c];
+            q[w][a][c] += c1 * sv1[w][a][c];
+          }
+    }
+    if (t < cnt) {
+      const int s0 = slot_of(t);
+      float sv0[W][A][3], yv0[W][A][3];
+#pragma unroll
+      for (int w = 0; w < W; ++w)
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sv0[w][a][c] = Sh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+            yv0[w][a][c] = Yh[hidx<T, A>(s0, a, c, lane + 32 * w)];
+          }
       float part = 0.f;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) part += yv[w][a][c] * q[w][a][c];
-      const float coef = at - r * warp_sum(part);
+          for (int c = 0; c < 3; ++c) part += yv0[w][a][c] * q[w][a][c];
+      const float c0 = alpha[t] - rho[s0] * warp_sum(part);
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) q[w][a][c] += coef * sv[w][a][c];
+          for (int c = 0; c < 3; ++c) q[w][a][c] += c0 * sv0[w][a][c];
     }
     float part = 0.f;
 #pragma unroll
@@ -592,10 +689,11 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 // hand over (a switch_gtol below the FP32 gradient noise).
 // ---------------------------------------------------------------------------
 template <int T, int A, typename P, int MODE>
-__device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
+__device__ __forceinline__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
                          typename P::XG (&g)[A][3], typename P::F& f,
                          typename P::V* __restrict__ Sh, typename P::V* __restrict__ Yh,
-                         typename P::V (&rho)[LJ_MAX_M], typename P::V (&gmv)[LJ_MAX_M], int& cnt,
+                         typename P::V (&rho)[LJ_MAX_M], typename P::V (&gmv)[LJ_MAX_M],
+                         typename P::V (&sup)[LJ_MAX_M], int& cnt,
                          int& head, int& iters,
                          int& evals, int& phase_iters, long long& vec, void* pos,
                          void* hbuf, const MinParams& p, long long t0, long long (&cyc)[2]) {
@@ -620,7 +718,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
     bool led = false;
     if constexpr (std::is_same<V, float>::value && T > 32 && T <= 128) {
       if (cnt > 0 && 12 * A * T + 4 <= 32 * n) {
-        dphi0 = (S)lead_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh, rho, gmv, g,
+        dphi0 = (S)lead_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh, rho, gmv, sup, g,
                                            static_cast<float*>(pos), d);
         vec += (long long)cnt * 3 * n;
         led = true;
@@ -890,7 +988,10 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
 
     // ---- curvature pair, then move ------------------------------------------
     V sv[A][3], yv[A][3];
-    V pr[2] = {(V)0, (V)0};
+    // s.y, y.y and s_prev.y (the newest stored pair's s against the new y:
+    // the superdiagonal entry the blocked two-loop recursion uses)
+    V pr[3] = {(V)0, (V)0, (V)0};
+    const int prev = cnt > 0 ? (head + cnt - 1 >= m ? head + cnt - 1 - m : head + cnt - 1) : -1;
 #pragma unroll
     for (int a = 0; a < A; ++a)
 #pragma unroll
@@ -899,6 +1000,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         yv[a][c] = (V)(gt[a][c] - g[a][c]);
         pr[0] += sv[a][c] * yv[a][c];
         pr[1] += yv[a][c] * yv[a][c];
+        if (prev >= 0) pr[2] += Sh[hidx<T, A>(prev, a, c, tm.rank)] * yv[a][c];
       }
     // stopping-test values of the new point (||g||_inf, deadline), reduced
     // in the same pass as the curvature pair's s.y and y.y
@@ -909,7 +1011,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
 #pragma unroll
       for (int c = 0; c < 3; ++c) mv[0] = fmax(mv[0], abs_nan_inf(gt[a][c]));
     mv[1] = (p.deadline > 0 && (clock64() - t0) > p.deadline) ? (XG)1 : (XG)0;
-    team_sum2_max2<T, V, XG>(tm, pr, mv);
+    team_sums_max2<T, V, XG>(tm, pr, mv);
     if (pr[0] > eps_mach<V>() * pr[1]) {
       int slot;
       if (cnt < m) {
@@ -929,6 +1031,7 @@ __device__ int run_phase(const Team<T>& tm, int n, typename P::XP (&x)[A][3],
         }
       rho[slot] = (V)1 / pr[0];      // rho = 1 / s.y and the scaling s.y / y.y, formed
       gmv[slot] = pr[0] / pr[1];     // once here instead of in every recursion step
+      sup[slot] = pr[2];             // s_prev . y (undefined for the oldest pair: unused)
     }
 #pragma unroll
     for (int a = 0; a < A; ++a)
@@ -969,7 +1072,7 @@ __device__ __forceinline__ int status_of(int code) {
 }
 
 template <int T, int A, bool MIXED>
-__device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const MinParams& p,
+__device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const MinParams& p,
                          void* hist, void* pos, void* hbuf, MinResult& r) {
   r.E = 0.0; r.status = ST_CONVERGED; r.iters = 0;
   r.evals32 = 0; r.evals64 = 0; r.evals_df = 0; r.iters32 = 0; r.iters64 = 0;
@@ -999,9 +1102,9 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       r.E = f; r.status = ST_NONFINITE; lap(r.cyc64); return;
     }
     if (gm < p.gtol) { r.E = f; lap(r.cyc64); return; }
-    double rho[LJ_MAX_M], gmv[LJ_MAX_M];
+    double rho[LJ_MAX_M], gmv[LJ_MAX_M], sup[LJ_MAX_M];
     double* Sh = (double*)hist;
-    const int code = run_phase<T, A, PrecF64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, rho, gmv, cnt,
+    const int code = run_phase<T, A, PrecF64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, rho, gmv, sup, cnt,
                                                  head, iters, r.evals64, r.iters64, r.vec64, pos,
                                                  hbuf, p, t0, cyc);
     r.E = f;
@@ -1011,7 +1114,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
   } else {
     float* Sh = (float*)hist;
     float* Yh = Sh + hstride;
-    float rho[LJ_MAX_M], gmv[LJ_MAX_M];
+    float rho[LJ_MAX_M], gmv[LJ_MAX_M], sup[LJ_MAX_M];
     int code = PH_SWITCH;
     float dummy32;
     // ---- tier 1: FP32 -------------------------------------------------------
@@ -1028,7 +1131,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       r.evals32 = 1;
       const float gm = grad_max<T, A, float>(tm, g32);
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
-        code = run_phase<T, A, PrecF32, 1>(tm, n, x32, g32, f32, Sh, Yh, rho, gmv, cnt, head,
+        code = run_phase<T, A, PrecF32, 1>(tm, n, x32, g32, f32, Sh, Yh, rho, gmv, sup, cnt, head,
                                            iters, r.evals32, r.iters32, r.vec32, pos, nullptr, p,
                                            t0, cyc);
         moved32 = r.iters32 > 0;
@@ -1064,7 +1167,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
           need_fp64 = true;               // confirm (and finish) in FP64
           break;
         }
-        code = run_phase<T, A, PrecDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, rho, gmv, cnt, head, iters,
+        code = run_phase<T, A, PrecDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, rho, gmv, sup, cnt, head, iters,
                                           r.evals_df, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
         if (code == PH_CONVERGED) {
           gm = 0.f;
@@ -1093,7 +1196,7 @@ __device__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const Mi
       if (gm < p.gtol) {
         r.E = f; r.iters = iters; r.status = ST_CONVERGED; lap(r.cyc64); return;
       }
-      code = run_phase<T, A, PrecF64m, 0>(tm, n, x64, g, f, Sh, Yh, rho, gmv, cnt, head, iters,
+      code = run_phase<T, A, PrecF64m, 0>(tm, n, x64, g, f, Sh, Yh, rho, gmv, sup, cnt, head, iters,
                                           r.evals64, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
       r.E = f;
       r.iters = iters;
