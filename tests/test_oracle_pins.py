@@ -445,3 +445,25 @@ def test_lj38_truncated_octahedron_is_oh_symmetric_and_lowest():
     starts = inputs.cube_starts(48, 38, 3.2, seed=inputs.workload_seed(1) + 77)
     _, ec, sc, _, _ = O.lbfgs_batch(starts, 48, uniform_n=38)
     assert (ec[sc == O.CONVERGED] > em + 1e-6).all()
+
+
+def test_golden_lj38_oh_fixture():
+    """tests/golden/lj38_oh_truncated_octahedron.txt (written by make_golden.py from
+    the oracle): the stored minimum still evaluates to its stored energy, is a
+    stationary point, and keeps the O_h symmetry the paper's Results give the LJ38
+    global minimum."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "lj38_oh_truncated_octahedron.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert rows[0][0] == "energy"
+    e_stored = float(rows[0][1])
+    p = np.array([[float(v) for v in r] for r in rows[1:]])
+    assert p.shape == (38, 3)
+    e, g = O.lj_energy_grad(p.reshape(-1))
+    assert abs(e - e_stored) <= 1e-12 * abs(e_stored)
+    assert np.abs(g).max() < 1e-6
+    assert abs(e_stored - (-173.928427)) < 1e-6
+    for m in oh_operations():
+        q = p @ m.T
+        d = np.linalg.norm(q[:, None, :] - p[None, :, :], axis=2).min(1)
+        assert d.max() < 1e-6
