@@ -36,7 +36,9 @@ _SO = os.path.join(_BUILD, "liblj_oracle.so")
 _SRC = [os.path.join(_HERE, "lj_oracle.c"), os.path.join(_HERE, "lj_oracle.h")]
 
 CONVERGED, MAXITER, LINESEARCH_FAIL, NONFINITE, TIMEOUT, BAD_INPUT = range(6)
-OBJ_LJ, OBJ_QUADRATIC, OBJ_ROSENBROCK = range(3)
+OBJ_LJ, OBJ_QUADRATIC, OBJ_ROSENBROCK, OBJ_POLY1D = range(4)
+LS_FAILED, LS_WOLFE, LS_FALLBACK = range(3)
+LS_LOG_MAX = 64
 
 _lock = threading.Lock()
 _lib = None
@@ -68,6 +70,18 @@ class Objective(C.Structure):
                 ("b", C.c_void_p), ("eps", C.c_double), ("sigma", C.c_double)]
 
 
+class LsLog(C.Structure):
+    _fields_ = [("f0", C.c_double), ("dphi0", C.c_double),
+                ("trial", (C.c_double * 3) * LS_LOG_MAX), ("n_trial", C.c_int32),
+                ("exit", C.c_int32)]
+
+
+class StepLog(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("f0", C.c_double), ("f", C.c_double),
+                ("dphi0", C.c_double), ("dphi", C.c_double), ("exit", C.c_int32),
+                ("retried", C.c_int32), ("n_trial", C.c_int32), ("pad", C.c_int32)]
+
+
 class BhParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("kT", C.c_double), ("target_rate", C.c_double),
                 ("interval", C.c_int32), ("factor", C.c_double), ("seed", C.c_uint64),
@@ -97,6 +111,14 @@ def _load():
             lib.orc_lbfgs_minimize.argtypes = [C.POINTER(Objective), P,
                                                C.POINTER(LbfgsParams), P, P, P, P]
             lib.orc_lbfgs_minimize.restype = C.c_int32
+            lib.orc_lbfgs_minimize_log.argtypes = [C.POINTER(Objective), P,
+                                                   C.POINTER(LbfgsParams), P, P, P, P, P,
+                                                   C.c_int32]
+            lib.orc_lbfgs_minimize_log.restype = C.c_int32
+            lib.orc_line_search.argtypes = [C.POINTER(Objective), P, P, C.c_double,
+                                            C.POINTER(LbfgsParams), P, P,
+                                            C.POINTER(LsLog), P]
+            lib.orc_line_search.restype = C.c_int32
             lib.orc_perturb.argtypes = [C.c_int64, P, C.c_double, C.c_uint64,
                                         C.c_uint32, C.c_uint32, C.c_uint32, P]
             lib.orc_perturb.restype = None
@@ -210,6 +232,58 @@ def minimize(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None, b=
     st = _load().orc_lbfgs_minimize(C.byref(obj), _ptr(x), C.byref(pc), C.byref(f),
                                     C.byref(it), C.byref(ne), _ptr(work))
     return x, float(f.value), int(st), int(it.value), int(ne.value)
+
+
+def minimize_log(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None, b=None,
+                 eps: float = 1.0, sigma: float = 1.0, max_steps: int = 20000):
+    """minimize() that also returns a record of every accepted step: a
+    structured array with alpha, f0, f, dphi0, dphi (phi'(alpha) along the
+    step's direction), exit (LS_WOLFE / LS_FALLBACK), retried, n_trial."""
+    p = params or MinParams()
+    x = _f64(x0).reshape(-1).copy()
+    n = x.size
+    Aa = _f64(A) if A is not None else None
+    ba = _f64(b) if b is not None else None
+    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma)
+    work = np.zeros((4 + 2 * p.m) * n + p.m + 1)
+    logs = (StepLog * max_steps)()
+    f = C.c_double()
+    it = C.c_int32()
+    ne = C.c_int32()
+    pc = p.c()
+    st = _load().orc_lbfgs_minimize_log(C.byref(obj), _ptr(x), C.byref(pc), C.byref(f),
+                                        C.byref(it), C.byref(ne), _ptr(work), logs, max_steps)
+    n_steps = min(int(it.value), max_steps)
+    rec = [{k: getattr(logs[i], k) for k, _ in StepLog._fields_ if k != "pad"}
+           for i in range(n_steps)]
+    return x, float(f.value), int(st), int(it.value), int(ne.value), rec
+
+
+def line_search(x, d, alpha1: float, kind: int = OBJ_POLY1D, params: MinParams | None = None,
+                A=None, b=None, eps: float = 1.0, sigma: float = 1.0):
+    """One strong-Wolfe line search of the oracle from x along d with first
+    trial alpha1.  Returns a dict: ok, alpha, f (accepted point), f0, dphi0,
+    trials (k x 3 array of alpha, phi, phi' in evaluation order; a final
+    re-evaluation of an earlier trial after an exhausted budget included)
+    and exit (LS_WOLFE, LS_FALLBACK or LS_FAILED)."""
+    p = params or MinParams()
+    x = _f64(x).reshape(-1)
+    d = _f64(d).reshape(-1)
+    n = x.size
+    Aa = _f64(A) if A is not None else None
+    ba = _f64(b) if b is not None else None
+    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma)
+    work = np.zeros(3 * n)
+    log = LsLog()
+    a = C.c_double()
+    f = C.c_double()
+    pc = p.c()
+    ok = _load().orc_line_search(C.byref(obj), _ptr(x), _ptr(d), alpha1, C.byref(pc),
+                                 C.byref(a), C.byref(f), C.byref(log), _ptr(work))
+    k = min(log.n_trial, LS_LOG_MAX)
+    trials = np.array([[log.trial[i][j] for j in range(3)] for i in range(k)]).reshape(-1, 3)
+    return {"ok": bool(ok), "alpha": float(a.value), "f": float(f.value), "f0": log.f0,
+            "dphi0": log.dphi0, "trials": trials, "exit": int(log.exit)}
 
 
 def _layout(n_cand, uniform_n, atom_off):

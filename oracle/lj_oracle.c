@@ -33,9 +33,14 @@
  * translation / rotation / permutation invariance, epsilon/sigma scaling law,
  * brute force on 2-4 atoms, quadratic and Rosenbrock minimisers, two-loop vs
  * explicit BFGS inverse-Hessian recursion, cubic interpolation on cubics,
- * strong-Wolfe property of accepted steps, Philox known-answer vectors,
- * Metropolis / adaptation properties, and a black-box cross-check against
- * scipy's L-BFGS-B.
+ * Philox known-answer vectors, Metropolis / adaptation properties, and a
+ * black-box cross-check against scipy's L-BFGS-B.  The line search is pinned
+ * in tests/test_oracle_linesearch.py: one-dimensional lines whose correct
+ * trial sequence follows from N&W Alg. 3.5/3.6 by hand (doubling, exact
+ * zoom on quadratics, strong versus weak curvature, alpha_max, non-finite
+ * trials, the exhausted-budget rule), zoom's bracket invariants checked on
+ * every trial of quartic, Rosenbrock and LJ lines, and both strong-Wolfe
+ * conditions on every step a minimisation accepts.
  */
 #include <math.h>
 #include <float.h>
@@ -175,6 +180,18 @@ static double orc_objective_eval(const orc_objective* o, const double* x, double
         }
         return f;
     }
+    if (o->kind == ORC_OBJ_POLY1D) {
+        /* one variable: f = c0 + c1 x + c2 x^2 + c3 x^3 + c4 x^4 (b = c),
+         * non-finite beyond x > A[0] when A is given */
+        const double* c = o->b;
+        double t = x[0];
+        if (o->A && t > o->A[0]) {
+            g[0] = NAN;
+            return INFINITY;
+        }
+        g[0] = c[1] + t * (2.0 * c[2] + t * (3.0 * c[3] + t * 4.0 * c[4]));
+        return c[0] + t * (c[1] + t * (c[2] + t * (c[3] + t * c[4])));
+    }
     /* extended Rosenbrock: sum over pairs (x_{2i}, x_{2i+1}) */
     double f = 0.0;
     for (int64_t i = 0; i < n; ++i) g[i] = 0.0;
@@ -286,10 +303,24 @@ static double orc_phi(const orc_objective* o, int64_t n, const double* x, const 
 /* best point that satisfied sufficient decrease is taken, if there is one.   */
 /* On return 1, xt/gt/f_out hold the accepted point.                          */
 /* ------------------------------------------------------------------------- */
+/* Optional record of one line search: every trial (alpha, phi, phi') in the
+ * order evaluated, and how it ended.  Only tests read it. */
+static void orc_log_trial(orc_ls_log* log, double a, double f, double dp)
+{
+    if (!log) return;
+    if (log->n_trial < ORC_LS_LOG_MAX) {
+        log->trial[log->n_trial][0] = a;
+        log->trial[log->n_trial][1] = f;
+        log->trial[log->n_trial][2] = dp;
+    }
+    log->n_trial++;
+}
+
 static int orc_wolfe_search(const orc_objective* o, int64_t n, const double* x, double f0,
                             const double* d, double dphi0, double alpha1,
                             const orc_lbfgs_params* p, double* xt, double* gt,
-                            double* f_out, double* alpha_out, int32_t* nevals)
+                            double* f_out, double* alpha_out, int32_t* nevals,
+                            orc_ls_log* log)
 {
     const double c1 = p->c1, c2 = p->c2;
     int evals = 0;
@@ -299,11 +330,13 @@ static int orc_wolfe_search(const orc_objective* o, int64_t n, const double* x, 
     double lo = 0, f_lo = 0, dp_lo = 0, hi = 0, f_hi = 0, dp_hi = 0;
     double last_a = -1.0;
     double f, dp;
+    if (log) { log->n_trial = 0; log->exit = ORC_LS_FAILED; log->f0 = f0; log->dphi0 = dphi0; }
 
     for (int i = 1;; ++i) {
         if (evals >= p->max_ls) goto exhausted;
         f = orc_phi(o, n, x, d, a, xt, gt, &dp);
         ++evals;
+        orc_log_trial(log, a, f, dp);
         last_a = a;
         int armijo = isfinite(f) && (f <= f0 + c1 * a * dphi0);
         if (armijo && f < best_f) { best_f = f; best_a = a; }
@@ -314,6 +347,7 @@ static int orc_wolfe_search(const orc_objective* o, int64_t n, const double* x, 
         }
         if (fabs(dp) <= -c2 * dphi0) {
             *f_out = f; *alpha_out = a; *nevals += evals;
+            if (log) log->exit = ORC_LS_WOLFE;
             return 1;
         }
         if (dp >= 0.0) {
@@ -330,6 +364,7 @@ static int orc_wolfe_search(const orc_objective* o, int64_t n, const double* x, 
         double aj = orc_cubic_interpolate(lo, f_lo, dp_lo, hi, f_hi, dp_hi);
         f = orc_phi(o, n, x, d, aj, xt, gt, &dp);
         ++evals;
+        orc_log_trial(log, aj, f, dp);
         last_a = aj;
         int armijo = isfinite(f) && (f <= f0 + c1 * aj * dphi0);
         if (armijo && f < best_f) { best_f = f; best_a = aj; }
@@ -338,6 +373,7 @@ static int orc_wolfe_search(const orc_objective* o, int64_t n, const double* x, 
         } else {
             if (fabs(dp) <= -c2 * dphi0) {
                 *f_out = f; *alpha_out = aj; *nevals += evals;
+                if (log) log->exit = ORC_LS_WOLFE;
                 return 1;
             }
             if (dp * (hi - lo) >= 0.0) {
@@ -358,19 +394,60 @@ exhausted:
             f = best_f;
         }
         *f_out = f; *alpha_out = best_a; *nevals += evals;
+        if (log) log->exit = ORC_LS_FALLBACK;
         return 1;
     }
     *nevals += evals;
     return 0;
 }
 
+/* One line search from x along d with first trial alpha1, for tests: phi(0)
+ * and phi'(0) are evaluated here, then the search above runs with `log`.
+ * work must hold 3 n doubles.  Returns 1 when a step was accepted. */
+int32_t orc_line_search(const orc_objective* o, const double* x, const double* d,
+                        double alpha1, const orc_lbfgs_params* p, double* alpha_out,
+                        double* f_out, orc_ls_log* log, double* work)
+{
+    const int64_t n = o->n;
+    double* g0 = work;
+    double* xt = g0 + n;
+    double* gt = xt + n;
+    double f0 = orc_objective_eval(o, x, g0);
+    double dphi0 = orc_dot(n, g0, d);
+    int32_t ne = 0;
+    *alpha_out = 0.0;
+    *f_out = f0;
+    return orc_wolfe_search(o, n, x, f0, d, dphi0, alpha1, p, xt, gt, f_out, alpha_out, &ne,
+                            log);
+}
+
 /* ------------------------------------------------------------------------- */
 /* L-BFGS minimiser (Algorithm Overview step 2 read as unbounded L-BFGS).     */
 /* work must hold (4 + 2m) n + m doubles.                                     */
 /* ------------------------------------------------------------------------- */
+static int32_t orc_lbfgs_run(const orc_objective* o, double* x, const orc_lbfgs_params* p,
+                             double* f_out, int32_t* iters_out, int32_t* nevals_out,
+                             double* work, orc_step_log* slog, int32_t max_steps);
+
 int32_t orc_lbfgs_minimize(const orc_objective* o, double* x, const orc_lbfgs_params* p,
                            double* f_out, int32_t* iters_out, int32_t* nevals_out,
                            double* work)
+{
+    return orc_lbfgs_run(o, x, p, f_out, iters_out, nevals_out, work, NULL, 0);
+}
+
+/* The same minimisation, recording every accepted step in slog[0..max_steps)
+ * (tests only).  *n_steps receives the number of accepted steps. */
+int32_t orc_lbfgs_minimize_log(const orc_objective* o, double* x, const orc_lbfgs_params* p,
+                               double* f_out, int32_t* iters_out, int32_t* nevals_out,
+                               double* work, orc_step_log* slog, int32_t max_steps)
+{
+    return orc_lbfgs_run(o, x, p, f_out, iters_out, nevals_out, work, slog, max_steps);
+}
+
+static int32_t orc_lbfgs_run(const orc_objective* o, double* x, const orc_lbfgs_params* p,
+                             double* f_out, int32_t* iters_out, int32_t* nevals_out,
+                             double* work, orc_step_log* slog, int32_t max_steps)
 {
     const int64_t n = o->n;
     const int32_t m = p->m;
@@ -414,7 +491,10 @@ int32_t orc_lbfgs_minimize(const orc_objective* o, double* x, const orc_lbfgs_pa
             if (a1 > 1.0) a1 = 1.0;
         }
         double ft, at;
-        int ok = orc_wolfe_search(o, n, x, f, d, dphi0, a1, p, xt, gt, &ft, &at, &nevals);
+        orc_ls_log ls;
+        orc_ls_log* lsp = slog ? &ls : NULL;
+        int retried = 0;
+        int ok = orc_wolfe_search(o, n, x, f, d, dphi0, a1, p, xt, gt, &ft, &at, &nevals, lsp);
         if (!ok && cnt > 0) {              /* one retry along -g with no history */
             cnt = 0;
             for (int64_t i = 0; i < n; ++i) d[i] = -g[i];
@@ -422,11 +502,23 @@ int32_t orc_lbfgs_minimize(const orc_objective* o, double* x, const orc_lbfgs_pa
             double dn = sqrt(-dphi0);
             a1 = 1.0 / dn;
             if (a1 > 1.0) a1 = 1.0;
-            ok = orc_wolfe_search(o, n, x, f, d, dphi0, a1, p, xt, gt, &ft, &at, &nevals);
+            retried = 1;
+            ok = orc_wolfe_search(o, n, x, f, d, dphi0, a1, p, xt, gt, &ft, &at, &nevals, lsp);
         }
         if (!ok) {
             status = ORC_LINESEARCH_FAIL;
             break;
+        }
+        if (slog && iters < max_steps) {
+            orc_step_log* r = &slog[iters];
+            r->alpha = at;
+            r->f0 = f;
+            r->f = ft;
+            r->dphi0 = dphi0;
+            r->dphi = orc_dot(n, gt, d);
+            r->exit = ls.exit;
+            r->retried = retried;
+            r->n_trial = ls.n_trial;
         }
         /* new curvature pair s = x_{k+1} - x_k, y = g_{k+1} - g_k; it is
          * stored only if s^T y > eps_mach y^T y (curvature guard) */

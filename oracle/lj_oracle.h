@@ -15,13 +15,14 @@ extern "C" {
 enum { ORC_CONVERGED = 0, ORC_MAXITER = 1, ORC_LINESEARCH_FAIL = 2, ORC_NONFINITE = 3,
        ORC_TIMEOUT = 4, ORC_BAD_INPUT = 5 };
 
-enum { ORC_OBJ_LJ = 0, ORC_OBJ_QUADRATIC = 1, ORC_OBJ_ROSENBROCK = 2 };
+enum { ORC_OBJ_LJ = 0, ORC_OBJ_QUADRATIC = 1, ORC_OBJ_ROSENBROCK = 2, ORC_OBJ_POLY1D = 3 };
 
 typedef struct {
     int32_t kind;          /* ORC_OBJ_* */
     int64_t n;             /* number of variables (3N for LJ) */
-    const double* A;       /* quadratic only: n x n symmetric, row-major */
-    const double* b;       /* quadratic only: n */
+    const double* A;       /* quadratic: n x n symmetric, row-major;
+                              POLY1D: NULL, or A[0] = bound above which f = +inf */
+    const double* b;       /* quadratic: n; POLY1D: 5 coefficients c0..c4 */
     double eps, sigma;     /* LJ only */
 } orc_objective;
 
@@ -48,6 +49,25 @@ typedef struct {
     orc_lbfgs_params min;
 } orc_bh_params;
 
+/* record of one line search (tests only) */
+#define ORC_LS_LOG_MAX 64
+enum { ORC_LS_FAILED = 0, ORC_LS_WOLFE = 1, ORC_LS_FALLBACK = 2 };
+typedef struct {
+    double f0, dphi0;
+    double trial[ORC_LS_LOG_MAX][3];   /* alpha, phi(alpha), phi'(alpha) */
+    int32_t n_trial;
+    int32_t exit;                      /* ORC_LS_* */
+} orc_ls_log;
+
+/* record of one accepted L-BFGS step (tests only) */
+typedef struct {
+    double alpha, f0, f, dphi0, dphi;
+    int32_t exit;                      /* ORC_LS_WOLFE or ORC_LS_FALLBACK */
+    int32_t retried;                   /* accepted on the retry along -g */
+    int32_t n_trial;
+    int32_t pad;
+} orc_step_log;
+
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_u01(uint32_t a, uint32_t b);
 double orc_stream_uniform(uint64_t seed, uint32_t tag, uint32_t draw,
@@ -61,6 +81,12 @@ double orc_cubic_interpolate(double a, double fa, double ga, double b, double fb
 int32_t orc_lbfgs_minimize(const orc_objective* o, double* x, const orc_lbfgs_params* p,
                            double* f_out, int32_t* iters_out, int32_t* nevals_out,
                            double* work);
+int32_t orc_lbfgs_minimize_log(const orc_objective* o, double* x, const orc_lbfgs_params* p,
+                               double* f_out, int32_t* iters_out, int32_t* nevals_out,
+                               double* work, orc_step_log* slog, int32_t max_steps);
+int32_t orc_line_search(const orc_objective* o, const double* x, const double* d,
+                        double alpha1, const orc_lbfgs_params* p, double* alpha_out,
+                        double* f_out, orc_ls_log* log, double* work);
 
 /* perturbation of one candidate: out_c = x_c + step * (2 u_c - 1) */
 void orc_perturb(int64_t n_coords, const double* x, double step, uint64_t seed,
