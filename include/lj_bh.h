@@ -304,26 +304,33 @@ lj_status lj_ctx_autotune_batch(lj_ctx* ctx, const lj_batch* batch, const double
  * (Not part of the method: the paper has no counterpart; it only changes
  * where this library keeps its scratch memory.)
  *
- * Who needs it: code that records the call into a CUDA graph (cudaMalloc may
- * synchronise the device, which stream capture forbids), applications whose
- * memory manager has already reserved the device memory and does not allow
- * further cudaMalloc/cudaFree, and latency-critical loops that cannot pay for
- * an allocation.  It takes no lj_ctx (creating one allocates) and uses the
- * default tuning options.
+ * Who needs it: applications whose memory manager has already taken the
+ * device memory it is allowed and forbids further cudaMalloc/cudaFree (a
+ * framework's caching allocator, a pool sized once at start-up), code that
+ * runs where an allocation's implicit device synchronisation is not
+ * acceptable, and latency-critical loops that cannot pay for an allocation.
+ * It takes no lj_ctx (creating one allocates) and uses the default tuning
+ * options.
  *
  * Scratch: a fixed array of LJ_NOALLOC_SCRATCH_BYTES in the library's
- * device-global memory holds the work-queue counters, the size-bucket lists
- * of an uneven batch (6 x 4 bytes per candidate) and any L-BFGS history that
- * does not fit in shared memory.  Every GPU that loads the library holds
- * this array until the process exits.  When the history of all teams would
- * not fit, fewer teams are launched (each still drains the shared work
- * queue), so a large batch takes longer but still runs.  A batch whose
- * bucket lists, or whose smallest launch (one CTA), would not fit returns
- * LJ_ERR_NO_WORKSPACE (an uneven batch of more than ~690,000 candidates).
+ * device-global memory holds the work-queue counters (256 bytes), the
+ * size-bucket lists of an uneven batch (6 x 4 bytes per candidate) and any
+ * L-BFGS history that does not fit in shared memory.  Every GPU that loads
+ * the library holds this array until the process exits.
+ * Limits: an uneven batch of more than
+ * (LJ_NOALLOC_SCRATCH_BYTES - 256) / 24 = 699,040 candidates returns
+ * LJ_ERR_NO_WORKSPACE.  When the off-chip history of all teams would not fit
+ * in what is left, fewer teams are launched (each still drains the shared
+ * work queue), so the batch takes longer but still runs; for large clusters
+ * this caps the launch hard: a history slot holds 2 m x 3 x 1024 values for
+ * clusters of 513..1024 atoms (4 bytes each for LJ_PREC_MIXED, 8 for
+ * LJ_PREC_FP64), so with m = 20 about 34 (mixed) or 17 (FP64) teams run, on
+ * a small part of the GPU.  A batch whose smallest launch (one CTA) would not
+ * fit returns LJ_ERR_NO_WORKSPACE.
  *
  * Set-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Later calls use the cached address.
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Later calls use the cached address.
  *
  * Calls share the array: the counter is cleared at the start of every call
  * and the previous call's contents are otherwise left in place.  Calls that

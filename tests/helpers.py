@@ -7,10 +7,28 @@
   check properties of returned minima (||g||_inf, E(x) consistency).
 * grad_scale: the no-cancellation gradient scale ||(sum_j |c_ij d_ij|)_i||_2,
   the denominator that keeps relative gradient errors meaningful near minima.
+* record: keeps the achieved figures of a parity test (printed, and appended
+  to the file LJ_PARITY_REPORT names, if any).
 """
+import json
+import os
+
 import numpy as np
 
 SAME_BASIN_TOL = 1e-3
+
+
+def record(tag, **metrics):
+    """Print the achieved parity figures of a test and, when the environment
+    variable LJ_PARITY_REPORT names a file, append them to it as one JSON
+    line, so that a run keeps the numbers its assertions were checked on."""
+    clean = {k: (float(v) if isinstance(v, (np.floating, np.integer)) else v)
+             for k, v in metrics.items()}
+    print(f"[parity] {tag}: " + ", ".join(f"{k}={v}" for k, v in clean.items()))
+    path = os.environ.get("LJ_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": tag, **clean}) + "\n")
 
 
 def fingerprint(x):

@@ -16,7 +16,7 @@ import pytest
 import oracle as O
 from paper_2510_25938_gb300 import inputs as I
 from tests.helpers import (energy_scale, fingerprint, grad_scale, grad_scale_terms,
-                           numpy_energy_grad, same_basin)
+                           numpy_energy_grad, record, same_basin)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -80,14 +80,18 @@ def _eval_compare(lj, ctx, x, off, prec, xdtype, rel_e, rel_g):
     torch.cuda.synchronize()
     e = e.cpu().numpy()
     g = g.cpu().numpy().astype(np.float64)
+    worst_e = worst_g = 0.0
     for c in range(n_cand):
         a0, a1 = 3 * off[c], 3 * off[c + 1]
         if sizes[c] <= 1:
             assert e[c] == 0.0 and np.all(g[a0:a1] == 0)
             continue
+        worst_e = max(worst_e, abs(e[c] - e_ref[c]) / abs(e_ref[c]))
         assert abs(e[c] - e_ref[c]) <= rel_e * abs(e_ref[c]), (c, sizes[c], e[c], e_ref[c])
         scale = max(np.linalg.norm(g_ref[a0:a1]), grad_scale(xin[a0:a1]))
+        worst_g = max(worst_g, np.linalg.norm(g[a0:a1] - g_ref[a0:a1]) / scale)
         assert np.linalg.norm(g[a0:a1] - g_ref[a0:a1]) <= rel_g * scale, (c, sizes[c])
+    return worst_e, worst_g
 
 
 # sizes cross every team variant and leave ragged tails in each
@@ -97,12 +101,15 @@ RAGGED_SIZES = [0, 1, 2, 3, 13, 31, 32, 33, 38, 63, 64, 65, 100, 127, 128, 129, 
 
 def test_eval_fp64_ragged(lj, ctx):
     x, off = _uneven(RAGGED_SIZES, 11)
-    _eval_compare(lj, ctx, x, off, lj.LJ_PREC_FP64, torch.float64, FP64_REL_E, FP64_REL_E)
+    we, wg = _eval_compare(lj, ctx, x, off, lj.LJ_PREC_FP64, torch.float64, FP64_REL_E,
+                           FP64_REL_E)
+    record("eval_fp64_ragged", max_rel_E=we, max_rel_g=wg)
 
 
 def test_eval_fp32_ragged(lj, ctx):
     x, off = _uneven(RAGGED_SIZES, 12)
-    _eval_compare(lj, ctx, x, off, lj.LJ_PREC_FP32, torch.float32, MIX_REL_E, MIX_REL_E)
+    we, wg = _eval_compare(lj, ctx, x, off, lj.LJ_PREC_FP32, torch.float32, MIX_REL_E, MIX_REL_E)
+    record("eval_fp32_ragged", max_rel_E=we, max_rel_g=wg)
 
 
 def test_eval_fp32_math_on_fp64_input(lj, ctx):
@@ -143,9 +150,13 @@ def test_eval_jittered_minima_uniform_batch(lj, ctx, prec, xdt, rel):
     rel_e = np.abs(e - e_ref) / np.abs(e_ref)
     assert rel_e.max() <= rel
     g_ref = g_ref.reshape(n_cand, -1)
+    worst_g = 0.0
     for c in range(n_cand):
         scale = max(np.linalg.norm(g_ref[c]), grad_scale(xin[c]))
+        worst_g = max(worst_g, np.linalg.norm(g[c] - g_ref[c]) / scale)
         assert np.linalg.norm(g[c] - g_ref[c]) <= rel * scale
+    record(f"eval_jittered_minima_{'fp32' if prec else 'fp64'}", max_rel_E=rel_e.max(),
+           max_rel_g=worst_g)
 
 
 # (N, candidates): padded odd N, several tiles per CTA (the flat layout runs
@@ -182,6 +193,9 @@ def test_eval_flat_uniform_sizes(lj, ctx, n_atoms, n_cand, prec):
     err = np.linalg.norm(g - g_ref, axis=1)
     scale = np.array([grad_scale_terms(xr[c]) for c in range(n_cand)])
     assert (err <= rel * scale).all()
+    record(f"eval_flat_{n_atoms}_{'fp32' if prec else 'fp64'}",
+           max_E_err_over_scale=(np.abs(e - e_ref) / escale).max(),
+           max_g_err_over_scale=(err / scale).max())
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -259,9 +273,10 @@ def _minimise_gpu(lj, ctx, x, off=None, uniform_n=0, prec=0, **kw):
             ne.cpu().numpy(), lj.stats_dict(stats))
 
 
-def _compare_minima(x0, off, xg, eg, sg, xo, eo, so, abs_tol, rel_tol, min_same):
+def _compare_minima(x0, off, xg, eg, sg, xo, eo, so, abs_tol, rel_tol, min_same, tag):
     n_cand = off.size - 1
     n_same = n_both = 0
+    max_de = 0.0
     for c in range(n_cand):
         a0, a1 = 3 * off[c], 3 * off[c + 1]
         if a1 - a0 <= 3:
@@ -278,12 +293,27 @@ def _compare_minima(x0, off, xg, eg, sg, xo, eo, so, abs_tol, rel_tol, min_same)
             n_both += 1
             if same_basin(xg[a0:a1], xo[a0:a1]):
                 n_same += 1
+                max_de = max(max_de, abs(eg[c] - eo[c]))
                 assert abs(eg[c] - eo[c]) <= max(abs_tol, rel_tol * abs(eo[c])), \
                     (c, eg[c], eo[c])
     frac = n_same / max(n_both, 1)
-    print(f"same-basin fraction {n_same}/{n_both} = {frac:.3f}")
+    record(tag, same_basin=n_same, both_converged=n_both, same_basin_fraction=frac,
+           floor=min_same, max_abs_dE_same_basin=max_de,
+           gpu_converged_fraction=float((sg == O.CONVERGED).mean()),
+           oracle_converged_fraction=float((so == O.CONVERGED).mean()))
     assert frac >= min_same
     return frac
+
+
+# Floors just under the measured figures (48 starts each).  FP64 runs the
+# oracle's own algorithm: it parts from the oracle only where summation-order
+# rounding meets a near-tie of the line search (measured 48/48 LJ13, 46/48
+# LJ38).  The mixed path rounds its first, violent steps from overlapping
+# atoms in FP32, so it reaches other minima of the landscape from most cube
+# starts (measured 14/48 LJ13, 0/47 LJ38 in the same basin); its agreement is
+# the distribution check below and the same-basin energy bound.
+CUBE_SAME = {(13, 0): 0.95, (38, 0): 0.9, (13, 2): 0.2, (38, 2): 0.0}
+CUBE_CONVERGED = {(13, 0): 0.95, (38, 0): 0.95, (13, 2): 0.95, (38, 2): 0.9}
 
 
 @pytest.mark.parametrize("prec", [0, 2])
@@ -295,17 +325,21 @@ def test_minimise_cube_starts(lj, ctx, prec, n_atoms, side, cfg):
     xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, uniform_n=n_atoms, prec=prec)
     xo, eo, so, ito, neo = O.lbfgs_batch(x0, n_cand, uniform_n=n_atoms)
     assert np.all(np.isin(sg, [O.CONVERGED, O.LINESEARCH_FAIL]))
-    assert (sg == O.CONVERGED).mean() >= 0.85
+    assert (sg == O.CONVERGED).mean() >= CUBE_CONVERGED[(n_atoms, prec)]
     assert stats["minimisations"] == n_cand
     assert stats["converged"] == int((sg == O.CONVERGED).sum())
     # from random cube starts the first steps are huge and chaotic: the mixed
-    # path (FP32 rounding from the first step) ends in other valid minima, so
-    # there the minima are checked for validity and for not being worse in
+    # path (FP32 rounding from the first step) mostly ends in other valid
+    # minima, so there the minima are checked for validity, for the same
+    # energy where the basin is the same, and for not being worse in
     # distribution (mean energy within 3 standard errors of the oracle's)
+    tag = f"minimise_cube_starts_lj{n_atoms}_{'mixed' if prec else 'fp64'}"
     if prec == 0:
-        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, 0.0, FP64_REL_E, 0.6)
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, 0.0, FP64_REL_E,
+                        CUBE_SAME[(n_atoms, 0)], tag)
     else:
-        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL, 0.0, 0.0)
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL, 0.0,
+                        CUBE_SAME[(n_atoms, 2)], tag)
         ok = (sg == O.CONVERGED) & (so == O.CONVERGED)
         diff = eg[ok].mean() - eo[ok].mean()
         se = np.sqrt(eg[ok].var() / ok.sum() + eo[ok].var() / ok.sum())
@@ -357,12 +391,13 @@ def test_minimise_large_fcc(lj, ctx, prec, n_atoms, n_cand, n_oracle):
     xo, eo, so, _, _ = O.lbfgs_batch(x0[:n_oracle], n_oracle, uniform_n=n_atoms,
                                      params=O.MinParams(m=20))
     off_o = off[:n_oracle + 1]
+    tag = f"minimise_large_fcc_{n_atoms}_{'mixed' if prec else 'fp64'}"
     if prec == 0:
         _compare_minima(x0[:n_oracle].reshape(-1), off_o, xg[:3 * n_atoms * n_oracle],
-                        eg[:n_oracle], sg[:n_oracle], xo, eo, so, 0.0, FP64_REL_E, 1.0)
+                        eg[:n_oracle], sg[:n_oracle], xo, eo, so, 0.0, FP64_REL_E, 1.0, tag)
     else:
         _compare_minima(x0[:n_oracle].reshape(-1), off_o, xg[:3 * n_atoms * n_oracle],
-                        eg[:n_oracle], sg[:n_oracle], xo, eo, so, MIX_ABS_FINAL, 0.0, 1.0)
+                        eg[:n_oracle], sg[:n_oracle], xo, eo, so, MIX_ABS_FINAL, 0.0, 1.0, tag)
 
 
 def test_autotune_then_uneven_batch(lj):
@@ -426,10 +461,13 @@ def test_minimise_bh_trial_moves_lj38(lj, ctx, prec):
     off = np.arange(n_cand + 1) * 38
     xg, eg, sg, it, ne, stats = _minimise_gpu(lj, ctx, x0, uniform_n=38, prec=prec)
     xo, eo, so, _, _ = O.lbfgs_batch(x0, n_cand, uniform_n=38)
+    # measured: FP64 47/47, mixed 33/47 in the same basin
+    tag = f"minimise_bh_trial_moves_lj38_{'mixed' if prec else 'fp64'}"
     if prec == 0:
-        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, 0.0, FP64_REL_E, 0.7)
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, 0.0, FP64_REL_E, 0.95, tag)
     else:
-        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL, 0.0, 0.5)
+        _compare_minima(x0.reshape(-1), off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL, 0.0, 0.6,
+                        tag)
 
 
 @pytest.mark.parametrize("prec", [0, 2])
@@ -443,8 +481,10 @@ def test_minimise_uneven_ragged(lj, ctx, prec):
             assert sg[c] == O.CONVERGED and eg[c] == 0.0 and it[c] == 0
     for c, n, emin in [(2, 2, -1.0), (3, 4, -6.0)]:
         assert eg[c] == pytest.approx(emin, abs=1e-10)
+    # cube starts of 2..150 atoms, ten comparable: measured FP64 9/10, mixed 3/10
     _compare_minima(x0, off, xg, eg, sg, xo, eo, so, MIX_ABS_FINAL if prec else 0.0,
-                    0.0 if prec else FP64_REL_E, 0.3)
+                    0.0 if prec else FP64_REL_E, 0.2 if prec else 0.8,
+                    f"minimise_uneven_ragged_{'mixed' if prec else 'fp64'}")
 
 
 def test_minimise_is_deterministic(lj, ctx):
@@ -549,7 +589,8 @@ def _bh_compare(lj, ctx, n_walkers, n_atoms, side, K, n_steps, prec, seed, min_s
                 win = 0
         assert gs["e_cur"][w].item() == e_cur
     frac = strict / total
-    print(f"steps matching the oracle exactly (before any divergence): {strict}/{total}")
+    record(f"bh_lj{n_atoms}_k{K}_{'mixed' if prec else 'fp64'}", steps_matching=strict,
+           steps=total, fraction=frac, floor=min_strict)
     assert frac >= min_strict
     e_best = gs["e_best"].cpu().numpy()
     xb = gs["x_best"].cpu().numpy()
@@ -583,7 +624,8 @@ def test_bh_lj38_k8_mixed(lj, ctx):
     tro = O.bh_run(st, O.BhParamsPy(K=8, kT=0.8, seed=5, n_steps=3))
     te, teo = tr["trial_e"].cpu().numpy()[0], tro["trial_e"][0]
     same = np.abs(te - teo) <= MIX_ABS_FINAL
-    print(f"step-0 candidates in the oracle's minimum: {same.sum()}/{same.size}")
+    record("bh_lj38_k8_mixed_step0", same_energy=int(same.sum()), candidates=same.size,
+           fraction=same.mean(), floor=0.5)
     assert same.mean() >= 0.5
     assert np.all(tr["trial_status"].cpu().numpy() != O.NONFINITE)
     # selection and Metropolis are consistent with the GPU's own energies
@@ -663,6 +705,8 @@ def test_uneven_4096_full_size_sampled(lj, ctx):
     x_sub = np.concatenate([x0[3 * off[c]:3 * off[c + 1]] for c in sample])
     xo, eo, so, _, _ = O.lbfgs_batch(x_sub, sample.size, atom_off=sub_off)
     xg_sub = np.concatenate([xg[3 * off[c]:3 * off[c + 1]] for c in sample])
-    # cube starts: chaotic; validity for all, same-basin energy match where it occurs
+    # cube starts, mixed path: chaotic (see CUBE_SAME); validity for all, the
+    # same-basin energy bound where the basin is the same (measured 1/23)
     _compare_minima(x_sub, sub_off, xg_sub, eg[sample], sg[sample], xo, eo, so,
-                    MIX_ABS_FINAL, 0.0, 0.0)
+                    MIX_ABS_FINAL, 0.0, 0.0, "uneven_4096_sampled_mixed")
+    record("uneven_4096_full_size", converged_fraction=float((sg == O.CONVERGED).mean()))

@@ -1,9 +1,10 @@
 """lbfgs_minimize_batched_noalloc against lbfgs_minimize_batched.
 
 The no-allocation entry point is for callers that must not allocate device
-memory (a CUDA graph being captured, an application whose memory manager owns
-the device memory, latency-critical loops): it keeps its scratch in a fixed
-library array instead of a context workspace.  It must give the results of
+memory (an application whose memory manager owns the device memory, code
+where an allocation's device synchronisation is not acceptable,
+latency-critical loops): it keeps its scratch in a fixed library array
+instead of a context workspace.  It must give the results of
 the ordinary entry point, on two calls in a row (the scratch array is shared
 between calls and keeps the previous call's contents).  This file is named to
 run last, and passes on its own as well as after the rest of the suite.
@@ -93,3 +94,46 @@ def test_noalloc_matches_context_entry_point_on_two_calls(lj, prec, case):
             first = (xg, eg)
         else:                            # the second call repeats the first
             assert np.array_equal(first[0], xg) and np.array_equal(first[1], eg)
+
+
+def test_noalloc_large_clusters_with_capped_grid(lj):
+    """600-atom FP64 minimisations with m = 20: each team's history (2 m x 3 x
+    1024 doubles, ~983 KB) lives off chip, only ~17 slots fit in the scratch
+    array, so the launch is capped below the batch size and teams take several
+    candidates each from the queue.  Results equal the context entry point's,
+    twice in a row."""
+    n_cand, n_atoms = 20, 600
+    x0 = I.fcc_fragments(n_cand, n_atoms, 0.1, I.workload_seed(4) + 600).reshape(-1)
+    off = np.arange(n_cand + 1, dtype=np.int64) * n_atoms
+
+    def run(noalloc):
+        x = torch.as_tensor(x0, dtype=torch.float64, device="cuda").contiguous()
+        e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+        st = torch.empty(n_cand, dtype=torch.int32, device="cuda")
+        stats = lj.new_stats()
+        p = lj.LbfgsParams(prec=lj.LJ_PREC_FP64, m=20)
+        if noalloc:
+            lib = lj.load()
+            b = lj._Batch(n_cand, n_atoms, None, n_atoms)
+            pc = p.c()
+            rc = lib.lbfgs_minimize_batched_noalloc(C.byref(b), C.byref(pc), x.data_ptr(),
+                                                    e.data_ptr(), st.data_ptr(), None, None,
+                                                    stats.data_ptr(),
+                                                    torch.cuda.current_stream().cuda_stream)
+            assert rc == lj.LJ_OK
+        else:
+            ctx = lj.Ctx(0)
+            lj.lbfgs_minimize_batched(ctx, x, e, st, None, None, stats, n_cand=n_cand,
+                                      uniform_n=n_atoms, params=p)
+            torch.cuda.synchronize()
+            ctx.close()
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), e.cpu().numpy(), st.cpu().numpy(), lj.stats_dict(stats)
+
+    xr, er, sr, _ = run(False)
+    assert np.all(sr == 0)
+    for call in range(2):
+        xg, eg, sg, stats = run(True)
+        assert stats["minimisations"] == n_cand
+        assert np.array_equal(sg, sr)
+        assert np.all(np.abs(eg - er) <= FP64_REL_E * np.abs(er))
