@@ -162,7 +162,13 @@ def test_eval_jittered_minima_uniform_batch(lj, ctx, prec, xdt, rel):
 # (N, candidates): padded odd N, several tiles per CTA (the flat layout runs
 # 2 CTAs per SM over tiles of floor(512 / N) candidates), and the extremes of
 # the flat layout (N = 2: 256 candidates per tile; N = 511, 512: one)
-FLAT_CASES = [(2, 3000), (13, 12500), (37, 6000), (38, 4100), (150, 900), (511, 30), (512, 20)]
+FLAT_CASES = [(2, 3000), (13, 12500), (37, 6000), (38, 4100), (150, 900), (511, 30), (512, 20),
+              # the pair-once FP32 layout (N <= 48, four atoms a thread): one group
+              # (4), two groups with the split last shift (5, 8), odd / even ring
+              # lengths (9, 16, 17), its largest size (48) and the first one-sided
+              # size above it (49)
+              (4, 3000), (5, 3000), (8, 2500), (9, 2500), (16, 2000), (17, 2000), (48, 900),
+              (49, 900)]
 
 
 @pytest.mark.parametrize("prec", [1, 0])
