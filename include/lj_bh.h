@@ -153,7 +153,17 @@ typedef struct {
     double* best_trial_e;   /* [n_steps][W] energy of the selected candidate */
     uint8_t* accepted;      /* [n_steps][W] Metropolis outcome */
     double* stepsize;       /* [n_steps][W] step size used in that step */
+    uint8_t* near_tie;      /* [n_steps][W] 1 when the Metropolis decision sat within
+                               LJ_NEAR_TIE of its threshold: |dE| <= LJ_NEAR_TIE (energy
+                               units) or, for dE > 0, |u - exp(-dE/kT)| <= LJ_NEAR_TIE *
+                               exp(-dE/kT).  Another FP64 implementation (other summation
+                               order, another exp) may decide such a step the other way */
 } lj_bh_trace;
+
+/* Near-tie margin of the Metropolis test: far above the ~1e-12 by which two
+ * FP64 evaluations of the same minimum differ, far below what one trial move
+ * changes. */
+#define LJ_NEAR_TIE 1e-9
 
 /* Device-side work counters, accumulated (atomically) by a call; the caller
  * zeroes them.  Used for flop accounting and throughput. */

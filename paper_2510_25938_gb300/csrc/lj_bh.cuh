@@ -168,19 +168,23 @@ __global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhA
         const double e = *cl.map_shared_rank(my_e, kk);
         if (isfinite(e) && (kb < 0 || e < eb)) { kb = kk; eb = e; }
       }
-      int acc = 0, better = 0;
+      int acc = 0, better = 0, tie = 0;
       double e_sel = __longlong_as_double(0x7ff0000000000000LL);
       if (kb >= 0) {
         e_sel = eb;
         const double u = stream_u01(a.seed, 2u, 0u, 0u, s, wg);
         const double de = e_sel - sh->e_cur;
-        acc = (de <= 0.0) || (u < exp(-de / a.kT));
+        const double thr = de > 0.0 ? exp(-de / a.kT) : 1.0;
+        acc = (de <= 0.0) || (u < thr);
+        // a decision within rounding of its threshold (see LJ_NEAR_TIE)
+        tie = fabs(de) <= LJ_NEAR_TIE || (de > 0.0 && fabs(u - thr) <= LJ_NEAR_TIE * thr);
       }
       if (k == 0) {
         const size_t tw = (size_t)it * a.n_walkers + w;
         if (a.tr.best_trial_e) a.tr.best_trial_e[tw] = e_sel;
         if (a.tr.accepted) a.tr.accepted[tw] = (uint8_t)acc;
         if (a.tr.stepsize) a.tr.stepsize[tw] = step;
+        if (a.tr.near_tie) a.tr.near_tie[tw] = (uint8_t)tie;
       }
       if (acc) {
         sh->e_cur = e_sel;

@@ -65,7 +65,8 @@ class _State(C.Structure):
 class _Trace(C.Structure):
     _fields_ = [("trial_e", C.c_void_p), ("trial_status", C.c_void_p),
                 ("trial_iters", C.c_void_p), ("best_trial_e", C.c_void_p),
-                ("accepted", C.c_void_p), ("stepsize", C.c_void_p)]
+                ("accepted", C.c_void_p), ("stepsize", C.c_void_p),
+                ("near_tie", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -329,7 +330,9 @@ STATE_KEYS = (("x_cur", torch.float64), ("e_cur", torch.float64), ("x_best", tor
               ("win_accept", torch.int32), ("n_accept", torch.int32))
 TRACE_KEYS = (("trial_e", torch.float64), ("trial_status", torch.int32),
               ("trial_iters", torch.int32), ("best_trial_e", torch.float64),
-              ("accepted", torch.uint8), ("stepsize", torch.float64))
+              ("accepted", torch.uint8), ("stepsize", torch.float64),
+              ("near_tie", torch.uint8))
+LJ_NEAR_TIE = 1e-9
 
 
 def bh_step_batched(ctx: Ctx, state: dict, params: BhParams, trace: dict | None = None,
@@ -338,7 +341,8 @@ def bh_step_batched(ctx: Ctx, state: dict, params: BhParams, trace: dict | None 
 
     state: x_cur / x_best (W, 3N) float64, e_cur / e_best / stepsize (W,) float64,
     win_accept / n_accept (W,) int32.  trace (optional): trial_e / trial_status /
-    trial_iters (n_steps, W, K), best_trial_e / accepted / stepsize (n_steps, W)."""
+    trial_iters (n_steps, W, K), best_trial_e / accepted / stepsize / near_tie
+    (n_steps, W)."""
     for k, dt in STATE_KEYS:
         if state[k].dtype != dt:
             raise ValueError(f"state[{k}] must be {dt}")
@@ -363,4 +367,5 @@ def new_trace(n_steps: int, n_walkers: int, K: int, device=None) -> dict:
             "trial_iters": torch.empty((n_steps, n_walkers, K), dtype=torch.int32, device=dev),
             "best_trial_e": torch.empty((n_steps, n_walkers), dtype=torch.float64, device=dev),
             "accepted": torch.empty((n_steps, n_walkers), dtype=torch.uint8, device=dev),
-            "stepsize": torch.empty((n_steps, n_walkers), dtype=torch.float64, device=dev)}
+            "stepsize": torch.empty((n_steps, n_walkers), dtype=torch.float64, device=dev),
+            "near_tie": torch.empty((n_steps, n_walkers), dtype=torch.uint8, device=dev)}
