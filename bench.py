@@ -56,7 +56,9 @@ N_ATOMS, WALKERS, K = 38, 64, 8
 BH_PER_LAUNCH = 10          # BH steps per bench step (one adaptation window)
 SIDE, STEP0, KT = 3.2, 0.4, 0.8
 # MIXED precision policy parameter of this workload: the FP32 tier's gradient
-# threshold (swept on LJ38 BH: 1e-3 168k, 3e-4 179k, 1e-4 183k converged/s)
+# threshold (swept on LJ38 BH: 1e-3 168k, 3e-4 179k, 1e-4 183k converged/s);
+# the bench runs lj_ctx_autotune_bh on the workload first and passes 0
+# (automatic: the tuned value) unless --no-tune, which passes this one
 SWITCH_GTOL = 1e-4
 CONFIG_ID = 1
 WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per BH step (512 L-BFGS "
@@ -89,6 +91,9 @@ def parse():
     ap.add_argument("--micro-only", action="store_true",
                     help="run only the evaluation microbench and print its JSON")
     ap.add_argument("--micro-repeats", type=int, default=100)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip lj_ctx_autotune_bh: library default team and history placement, "
+                         "switch_gtol 1e-4")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline, FP64 path and e2e only (no error, K-sweep, search-quality "
                          "or other-workload blocks)")
@@ -661,13 +666,21 @@ def run_cuda(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def bh_params(prec, k=K):
+    def bh_params(prec, k=K, sg=SWITCH_GTOL):
         return L.BhParams(K=k, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH, walker0=walker0,
-                          min=L.LbfgsParams(prec=prec, switch_gtol=SWITCH_GTOL))
+                          min=L.LbfgsParams(prec=prec, switch_gtol=sg))
+
+    # the library's autotuner picks the BH team, switch_gtol and history
+    # placement on copies of this workload's walkers (untimed set-up)
+    tuned = None
+    sg_run = SWITCH_GTOL
+    if not args.no_tune and not args.profile:
+        tuned = ctx.autotune_bh(init_state(), bh_params(L.LJ_PREC_MIXED, sg=0.0))
+        sg_run = 0.0
 
     def timed_run(prec, n_steps, warmup):
         state = init_state()
-        p = bh_params(prec)
+        p = bh_params(prec, sg=sg_run)
         for s in range(warmup):
             p.step0 = s * BH_PER_LAUNCH
             L.bh_step_batched(ctx, state, p)
@@ -698,7 +711,7 @@ def run_cuda(args):
         back, all between the step's CUDA events."""
         dstate = init_state()
         host = {k: v.cpu().pin_memory() for k, v in dstate.items()}
-        p = bh_params(prec)
+        p = bh_params(prec, sg=sg_run)
         stats = L.new_stats(dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -786,7 +799,11 @@ def run_cuda(args):
         "config": {"workload": WORKLOAD, "n_atoms": N_ATOMS, "walkers_per_gpu": WALKERS, "K": K,
                    "bh_steps_per_step": BH_PER_LAUNCH,
                    "minimisations_per_step": WALKERS * K * BH_PER_LAUNCH * world,
-                   "precision": "mixed", "switch_gtol": SWITCH_GTOL,
+                   "precision": "mixed",
+                   "switch_gtol": tuned["switch_gtol"] if tuned else SWITCH_GTOL,
+                   "autotuned": ({"team": tuned["team"], "switch_gtol": tuned["switch_gtol"],
+                                  "history_global": tuned["history_global"]}
+                                 if tuned else None),
                    "l2": "flushed (256 MiB write) between timed steps"},
         "minimisations_per_s": mins / t_dev,
         "converged_fraction": conv / max(mins, 1),

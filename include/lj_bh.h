@@ -198,9 +198,18 @@ typedef enum {
     LJ_OPT_F32_HANDOVER = 3, /* MIXED: below this many FP32 ulps of |E| of predicted
                                 decrease -alpha phi'(0), the FP32 phase accepts
                                 steps on the gradient alone (1..4096; 0 = default 4) */
-    LJ_OPT_DF_HANDOVER = 4   /* MIXED: below this many 2^-48 |E| of predicted
+    LJ_OPT_DF_HANDOVER = 4,  /* MIXED: below this many 2^-48 |E| of predicted
                                 decrease, the double-float polish accepts steps on
                                 the gradient alone (1..65536; 0 = default 32) */
+    LJ_OPT_HISTORY = 5,      /* L-BFGS history placement, both minimising calls:
+                                0 (automatic: the autotuned choice, else shared memory
+                                when a CTA's shared memory stays within ~100 KB),
+                                1 global memory always, 2 automatic ignoring the
+                                autotuner.  Results do not depend on it */
+    LJ_OPT_DF_EVAL = 6       /* MIXED double-float evaluations of clusters above 256
+                                atoms: 0 (automatic: the autotuned choice, else 32 x 32
+                                tiles taking each pair once), 1 one-sided rows (each
+                                pair from both atoms), 2 tiles */
 } lj_option;
 
 const char* lj_status_string(lj_status s);
@@ -275,7 +284,10 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_par
  *   bucket's upper size, history m, precision prec) twice; the second,
  *   timed run decides by converged minimisations per second.  For MIXED the
  *   same batch then runs with switch_gtol 1e-3, 3e-4 and 1e-4 on the chosen
- *   team, and the fastest is kept.
+ *   team, and the fastest is kept; then, where they are alternatives, the
+ *   history in global memory instead of shared memory, and (MIXED, buckets
+ *   above 256 atoms) one-sided double-float rows instead of tiles.  The
+ *   whole entry can be read back with lj_ctx_get_tuning.
  *   out_team         [LJ_TUNE_BUCKETS] chosen team sizes, 0 beyond max_n's
  *                    bucket (may be NULL).
  *   out_switch_gtol  [LJ_TUNE_BUCKETS] chosen switch_gtol (MIXED), 0 beyond
@@ -291,8 +303,45 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_par
  * previous choices.
  */
 #define LJ_TUNE_BUCKETS 6
+#define LJ_TUNE_BH LJ_TUNE_BUCKETS   /* lj_ctx_get_tuning: the bh_step_batched entry */
+
+/* One entry of a context's tuning table. */
+typedef struct {
+    int32_t team;            /* threads per candidate (0: default shape) */
+    double switch_gtol;      /* MIXED FP32-tier hand-over gradient (0: library default) */
+    int32_t history_global;  /* 1: L-BFGS history in global memory */
+    int32_t df_one_sided;    /* 1: one-sided double-float rows instead of tiles */
+    int32_t tuned;           /* 1 once an autotuning call has set this entry */
+} lj_tuning;
 lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision prec,
                           int32_t* out_team, double* out_switch_gtol, void* stream);
+
+/*
+ * lj_ctx_get_tuning -- the context's tuning entry for size bucket `bucket`
+ * (0 .. LJ_TUNE_BUCKETS-1, lbfgs_minimize_batched) or LJ_TUNE_BH
+ * (bh_step_batched).  Errors: INVALID_ARG (bucket out of range, NULL out).
+ */
+lj_status lj_ctx_get_tuning(const lj_ctx* ctx, int32_t bucket, lj_tuning* out);
+
+/*
+ * lj_ctx_autotune_bh -- tune bh_step_batched on the caller's own walkers.
+ * (A tuning aid of this library, not part of the paper's method.)
+ * Copies of `state` (left unchanged) run p->n_steps Basin Hopping steps
+ * (p as given: K, kT, seed, ...; p->min.prec FP64 or MIXED) twice for each
+ * choice -- the first run a warm-up, the second timed by converged
+ * minimisations per second -- choosing in turn the threads per candidate
+ * (32, 64 or 128 for clusters of up to 64 atoms; the default shape above),
+ * for MIXED the FP32 tier's switch_gtol (1e-3, 3e-4, 1e-4), and the history
+ * placement (shared memory when it fits, or global memory).  Later
+ * bh_step_batched calls on this ctx use the chosen team and placement
+ * unless LJ_OPT_BH_TEAM / LJ_OPT_HISTORY are set, and the chosen
+ * switch_gtol wherever p->min.switch_gtol = 0.  *out receives the choice
+ * (may be NULL).  A setup call like lj_ctx_autotune: it allocates device
+ * memory, may grow the workspace and synchronises `stream`.
+ * Errors: INVALID_ARG (as bh_step_batched; n_steps < 1), UNSUPPORTED, CUDA.
+ */
+lj_status lj_ctx_autotune_bh(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_params* p,
+                             lj_tuning* out, void* stream);
 
 /*
  * lj_ctx_autotune_batch -- the same choice for one size bucket, measured on

@@ -26,6 +26,15 @@ struct lj_ctx {
   int lbfgs_team = 0;                  // LJ_OPT_LBFGS_TEAM (0 = automatic)
   int tune_team[ljh::kMaxBuckets] = {};  // lj_ctx_autotune: team per size bucket (0 = none)
   double tune_sg[ljh::kMaxBuckets] = {}; // ... and MIXED switch_gtol per bucket (0 = none)
+  int tune_hist[ljh::kMaxBuckets] = {};  // ... history in global memory (1) per bucket
+  int tune_df[ljh::kMaxBuckets] = {};    // ... one-sided double-float rows (1) per bucket
+  bool tuned[ljh::kMaxBuckets] = {};
+  int hist_opt = 0;                    // LJ_OPT_HISTORY
+  int df_opt = 0;                      // LJ_OPT_DF_EVAL
+  int bh_tune_team = 0;                // lj_ctx_autotune_bh choices
+  double bh_tune_sg = 0.0;
+  int bh_tune_hist = 0;
+  bool bh_tuned = false;
   int f32_handover = 4;                // LJ_OPT_F32_HANDOVER (FP32 ulps of |E|)
   int df_handover = 32;                // LJ_OPT_DF_HANDOVER (2^-48 |E| units)
   std::string last_error;
@@ -165,6 +174,19 @@ int bucket_of(int n) {
 // size bucket holding `bucket_n` atoms, else kDefaultSwitchGtol
 constexpr double kDefaultSwitchGtol = 1e-3;
 
+// history placement and double-float evaluation form of a size bucket: the
+// option when set, else the autotuned choice (LJ_OPT_HISTORY / LJ_OPT_DF_EVAL)
+bool hist_global_for(const lj_ctx* ctx, int bucket) {
+  if (ctx->hist_opt == 1) return true;
+  if (ctx->hist_opt == 2 || bucket < 0) return false;
+  return ctx->tune_hist[bucket] != 0;
+}
+int df_one_sided_for(const lj_ctx* ctx, int bucket) {
+  if (ctx->df_opt == 1) return 1;
+  if (ctx->df_opt == 2 || bucket < 0) return 0;
+  return ctx->tune_df[bucket];
+}
+
 ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p, int bucket_n = 0) {
   ljh::MinParamsH h;
   h.f32_resolution = ctx->f32_handover * 5.9604644775390625e-8;    // ulps of 2^-24
@@ -177,6 +199,7 @@ ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p, int bucket_
     h.switch_gtol = t > 0.0 ? t : kDefaultSwitchGtol;
   }
   h.k = ljh::make_consts(p->eps, p->sigma);
+  h.df_one_sided = df_one_sided_for(ctx, bucket_n > 0 ? bucket_of(bucket_n) : -1);
   return h;
 }
 
@@ -288,6 +311,14 @@ lj_status lj_ctx_set_option(lj_ctx* ctx, lj_option opt, int64_t value) {
       if (value < 0 || value > 65536) return fail(ctx, LJ_ERR_INVALID_ARG, "DF handover 0..65536");
       ctx->df_handover = value ? (int)value : 32;
       return LJ_OK;
+    case LJ_OPT_HISTORY:
+      if (value < 0 || value > 2) return fail(ctx, LJ_ERR_INVALID_ARG, "history option 0, 1 or 2");
+      ctx->hist_opt = (int)value;
+      return LJ_OK;
+    case LJ_OPT_DF_EVAL:
+      if (value < 0 || value > 2) return fail(ctx, LJ_ERR_INVALID_ARG, "DF evaluation option 0, 1 or 2");
+      ctx->df_opt = (int)value;
+      return LJ_OK;
   }
   return fail(ctx, LJ_ERR_INVALID_ARG, "unknown option");
 }
@@ -352,8 +383,9 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   const int mixed = p->prec == LJ_PREC_MIXED;
   auto plan_for = [&](int bound, ljh::Plan* pl) {
     const int team = ctx->lbfgs_team ? ctx->lbfgs_team : ctx->tune_team[bucket_of(bound)];
-    return mixed ? ljh::lbfgs_plan_mixed(bound, p->m, batch->n_cand, ctx->device, team, pl)
-                 : ljh::lbfgs_plan_fp64(bound, p->m, batch->n_cand, ctx->device, team, pl);
+    const bool hg = hist_global_for(ctx, bucket_of(bound));
+    return mixed ? ljh::lbfgs_plan_mixed(bound, p->m, batch->n_cand, ctx->device, team, pl, hg)
+                 : ljh::lbfgs_plan_fp64(bound, p->m, batch->n_cand, ctx->device, team, pl, hg);
   };
   if (batch->uniform_n == 0 && max_n > 32 && batch->n_cand > 1) {
     // Uneven batch spanning several size classes: sort candidates into size
@@ -459,11 +491,18 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
   const int mixed = p->min.prec == LJ_PREC_MIXED;
+  // team, history placement and switch_gtol: the options when set, else
+  // the choices of lj_ctx_autotune_bh
+  const int team = ctx->bh_team ? ctx->bh_team : (ctx->bh_tuned ? ctx->bh_tune_team : 0);
+  const bool hg = ctx->hist_opt == 1 || (ctx->hist_opt == 0 && ctx->bh_tuned && ctx->bh_tune_hist);
+  lj_lbfgs_params minp = p->min;
+  if (!(minp.switch_gtol > 0.0) && ctx->bh_tuned && ctx->bh_tune_sg > 0.0)
+    minp.switch_gtol = ctx->bh_tune_sg;
   ljh::Plan plan;
-  cudaError_t e = mixed ? ljh::bh_plan_mixed(s->n_atoms, p->min.m, s->n_walkers, p->K,
-                                             ctx->bh_team, &plan)
-                        : ljh::bh_plan_fp64(s->n_atoms, p->min.m, s->n_walkers, p->K,
-                                            ctx->bh_team, &plan);
+  cudaError_t e = mixed ? ljh::bh_plan_mixed(s->n_atoms, p->min.m, s->n_walkers, p->K, team,
+                                             &plan, hg)
+                        : ljh::bh_plan_fp64(s->n_atoms, p->min.m, s->n_walkers, p->K, team,
+                                            &plan, hg);
   if (e == cudaErrorNotSupported)
     return fail(ctx, LJ_ERR_UNSUPPORTED,
                 "bh_step_batched supports clusters of up to 256 atoms in this build");
@@ -478,7 +517,7 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   a.K = p->K; a.kT = p->kT; a.target_rate = p->target_rate; a.factor = p->factor;
   a.interval = p->interval; a.seed = p->seed; a.step0 = p->step0; a.n_steps = p->n_steps;
   a.walker0 = p->walker0;
-  a.p = to_host(ctx, &p->min);
+  a.p = to_host(ctx, &minp);
   a.mixed = mixed;
   if (trace) {
     a.tr = *trace;
@@ -517,19 +556,26 @@ struct Tuner {
   double* e = nullptr;
   lj_stats* st = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  int saved_team;
-  bool saved_reserved;
+  int saved_team, saved_bh_team, saved_hist, saved_df;
+  bool saved_reserved, saved_bh_tuned;
   Tuner(lj_ctx* c, void* strm)
       : ctx(c), s((cudaStream_t)strm), stream(strm), saved_team(c->lbfgs_team),
-        saved_reserved(c->reserved) {
+        saved_bh_team(c->bh_team), saved_hist(c->hist_opt), saved_df(c->df_opt),
+        saved_reserved(c->reserved), saved_bh_tuned(c->bh_tuned) {
     ctx->reserved = false;                // tuning batches may grow the workspace
+    ctx->hist_opt = 2;                    // tuning runs ignore earlier tuned choices
+    ctx->df_opt = 2;
   }
   ~Tuner() {
     cudaFree(x); cudaFree(x0); cudaFree(e); cudaFree(st);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     ctx->lbfgs_team = saved_team;
+    ctx->bh_team = saved_bh_team;
+    ctx->hist_opt = saved_hist;
+    ctx->df_opt = saved_df;
     ctx->reserved = saved_reserved;
+    ctx->bh_tuned = saved_bh_tuned;
   }
   lj_status alloc(size_t coords, int64_t n_cand) {
     if (cudaMalloc(&x, coords * sizeof(double)) != cudaSuccess ||
@@ -566,8 +612,12 @@ struct Tuner {
     *out = ms > 0.f ? (double)conv / ms : 0.0;
     return LJ_OK;
   }
-  // the team size, then (MIXED) the switch_gtol of bucket b on the starts in x0
-  lj_status bucket(int b, int64_t nc, int nt, int m, lj_precision prec, int* team, double* sg) {
+  // the team size, then (MIXED) the switch_gtol of bucket b on the starts in
+  // x0, then the history placement (where shared memory holds it, global
+  // memory is tried) and, for MIXED buckets above 256 atoms, one-sided
+  // double-float rows against tiles
+  lj_status bucket(int b, int64_t nc, int nt, int m, lj_precision prec, int* team, double* sg,
+                   int* hist, int* df) {
     lj_lbfgs_params p;
     p.m = m; p.gtol = 1e-6; p.max_iter = 15000; p.max_ls = 20; p.c1 = 1e-3; p.c2 = 0.9;
     p.alpha_max = 1e10; p.prec = prec; p.switch_gtol = kDefaultSwitchGtol;
@@ -583,8 +633,8 @@ struct Tuner {
       }
     }
     *sg = 0.0;
+    double best = -1.0;
     if (prec == LJ_PREC_MIXED) {
-      double best = -1.0;
       for (double v : kSgChoices) {
         p.switch_gtol = v;
         double r = 0.0;
@@ -592,6 +642,34 @@ struct Tuner {
         if (rc != LJ_OK) return rc;
         if (r > best) { best = r; *sg = v; }
       }
+      p.switch_gtol = *sg;
+    } else {
+      lj_status rc = rate(p, nc, nt, *team, &best);
+      if (rc != LJ_OK) return rc;
+    }
+    *hist = 0;
+    *df = 0;
+    ljh::Plan pl;
+    cudaError_t e = prec == LJ_PREC_MIXED
+                        ? ljh::lbfgs_plan_mixed(nt, m, nc, ctx->device, *team, &pl, false)
+                        : ljh::lbfgs_plan_fp64(nt, m, nc, ctx->device, *team, &pl, false);
+    if (e != cudaSuccess) return fail(ctx, LJ_ERR_CUDA, "autotune: plan failed");
+    if (pl.hist_on_chip) {                 // the alternative: history in global memory
+      ctx->hist_opt = 1;
+      double r = 0.0;
+      lj_status rc = rate(p, nc, nt, *team, &r);
+      ctx->hist_opt = 2;
+      if (rc != LJ_OK) return rc;
+      if (r > best) { best = r; *hist = 1; }
+    }
+    if (prec == LJ_PREC_MIXED && nt > 256) {   // tiles (default) against one-sided rows
+      ctx->hist_opt = *hist ? 1 : 2;
+      ctx->df_opt = 1;
+      double r = 0.0;
+      lj_status rc = rate(p, nc, nt, *team, &r);
+      ctx->df_opt = 2;
+      if (rc != LJ_OK) return rc;
+      if (r > best) { best = r; *df = 1; }
     }
     return LJ_OK;
   }
@@ -618,6 +696,7 @@ lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision pr
   const int nb = bucket_of(max_n) + 1;
   int team[ljh::kMaxBuckets] = {};
   double sg[ljh::kMaxBuckets] = {};
+  int hist[ljh::kMaxBuckets] = {}, df[ljh::kMaxBuckets] = {};
   {
     Tuner tu(ctx, stream);
     size_t max_x = 0;
@@ -635,13 +714,16 @@ lj_status lj_ctx_autotune(lj_ctx* ctx, int32_t max_n, int32_t m, lj_precision pr
         rc = fail(ctx, LJ_ERR_CUDA, "autotune: start generation failed");
         break;
       }
-      rc = tu.bucket(b, kTuneCand[b], nt, m, prec, &team[b], &sg[b]);
+      rc = tu.bucket(b, kTuneCand[b], nt, m, prec, &team[b], &sg[b], &hist[b], &df[b]);
     }
   }
   if (rc != LJ_OK) return rc;
   for (int b = 0; b < ljh::kMaxBuckets; ++b) {
     ctx->tune_team[b] = b < nb ? team[b] : 0;
     ctx->tune_sg[b] = b < nb ? sg[b] : 0.0;
+    ctx->tune_hist[b] = b < nb ? hist[b] : 0;
+    ctx->tune_df[b] = b < nb ? df[b] : 0;
+    ctx->tuned[b] = b < nb;
     if (out_team) out_team[b] = ctx->tune_team[b];
     if (out_switch_gtol) out_switch_gtol[b] = ctx->tune_sg[b];
   }
@@ -663,7 +745,7 @@ lj_status lj_ctx_autotune_batch(lj_ctx* ctx, const lj_batch* batch, const double
   const int nt = batch->uniform_n;
   const int b = bucket_of(nt);
   const int64_t nc = std::min<int64_t>(batch->n_cand, max_sample);
-  int team = 0;
+  int team = 0, hist = 0, df = 0;
   double sg = 0.0;
   {
     Tuner tu(ctx, stream);
@@ -672,13 +754,147 @@ lj_status lj_ctx_autotune_batch(lj_ctx* ctx, const lj_batch* batch, const double
         cudaMemcpyAsync(tu.x0, d_x, (size_t)nc * 3 * nt * sizeof(double),
                         cudaMemcpyDeviceToDevice, tu.s) != cudaSuccess)
       rc = fail(ctx, LJ_ERR_CUDA, "autotune_batch: copying the sample failed");
-    if (rc == LJ_OK) rc = tu.bucket(b, nc, nt, m, prec, &team, &sg);
+    if (rc == LJ_OK) rc = tu.bucket(b, nc, nt, m, prec, &team, &sg, &hist, &df);
   }
   if (rc != LJ_OK) return rc;
   ctx->tune_team[b] = team;
   ctx->tune_sg[b] = sg;
+  ctx->tune_hist[b] = hist;
+  ctx->tune_df[b] = df;
+  ctx->tuned[b] = true;
   if (out_team) *out_team = team;
   if (out_switch_gtol) *out_switch_gtol = sg;
+  return LJ_OK;
+}
+
+lj_status lj_ctx_get_tuning(const lj_ctx* ctx, int32_t bucket, lj_tuning* out) {
+  if (!ctx || !out || bucket < 0 || bucket > LJ_TUNE_BH) return LJ_ERR_INVALID_ARG;
+  if (bucket == LJ_TUNE_BH) {
+    out->team = ctx->bh_tune_team;
+    out->switch_gtol = ctx->bh_tune_sg;
+    out->history_global = ctx->bh_tune_hist;
+    out->df_one_sided = 0;
+    out->tuned = ctx->bh_tuned ? 1 : 0;
+  } else {
+    out->team = ctx->tune_team[bucket];
+    out->switch_gtol = ctx->tune_sg[bucket];
+    out->history_global = ctx->tune_hist[bucket];
+    out->df_one_sided = ctx->tune_df[bucket];
+    out->tuned = ctx->tuned[bucket] ? 1 : 0;
+  }
+  return LJ_OK;
+}
+
+lj_status lj_ctx_autotune_bh(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_params* p,
+                             lj_tuning* out, void* stream) {
+  if (!ctx) return LJ_ERR_INVALID_ARG;
+  if (!state || !p) return fail(ctx, LJ_ERR_INVALID_ARG, "autotune_bh: state and params");
+  if (p->n_steps < 1 || state->n_walkers < 1 || state->n_atoms < 2)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "autotune_bh: n_steps >= 1, walkers >= 1, atoms >= 2");
+  if (p->min.prec != LJ_PREC_FP64 && p->min.prec != LJ_PREC_MIXED)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "autotune_bh: FP64 or MIXED");
+  if (!state->x_cur || !state->e_cur || !state->x_best || !state->e_best || !state->stepsize ||
+      !state->win_accept || !state->n_accept)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "autotune_bh: every state array is required");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, LJ_ERR_CUDA, "cudaSetDevice failed");
+  const int W = state->n_walkers, n = state->n_atoms;
+  const size_t xb = (size_t)W * 3 * n * sizeof(double), sb = (size_t)W * sizeof(double),
+               ib = (size_t)W * sizeof(int32_t);
+  const bool mixed = p->min.prec == LJ_PREC_MIXED;
+  int best_team = 0, best_hist = 0;
+  double best_sg = 0.0;
+  lj_status rc = LJ_OK;
+  {
+    Tuner tu(ctx, stream);
+    ctx->bh_tuned = false;                       // tuning runs use explicit choices
+    // working copies of the walkers (restored before every run)
+    lj_bh_state ws = *state;
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, 2 * xb + 3 * sb + 2 * ib) != cudaSuccess ||
+        cudaMalloc(&tu.st, sizeof(lj_stats)) != cudaSuccess ||
+        cudaEventCreate(&tu.ev0) != cudaSuccess || cudaEventCreate(&tu.ev1) != cudaSuccess) {
+      cudaFree(buf);
+      return fail(ctx, LJ_ERR_CUDA, "autotune_bh: allocation failed");
+    }
+    tu.x = static_cast<double*>(buf);            // freed with the tuner
+    unsigned char* q = static_cast<unsigned char*>(buf);
+    ws.x_cur = reinterpret_cast<double*>(q); q += xb;
+    ws.x_best = reinterpret_cast<double*>(q); q += xb;
+    ws.e_cur = reinterpret_cast<double*>(q); q += sb;
+    ws.e_best = reinterpret_cast<double*>(q); q += sb;
+    ws.stepsize = reinterpret_cast<double*>(q); q += sb;
+    ws.win_accept = reinterpret_cast<int32_t*>(q); q += ib;
+    ws.n_accept = reinterpret_cast<int32_t*>(q);
+    auto rate = [&](int team, double sg, int hist, double* r) -> lj_status {
+      ctx->bh_team = team;
+      ctx->hist_opt = hist ? 1 : 2;
+      lj_bh_params pp = *p;
+      if (mixed) pp.min.switch_gtol = sg;
+      float ms = 0.f;
+      unsigned long long conv = 0;
+      for (int rep = 0; rep < 2; ++rep) {        // the first run is a warm-up
+        cudaMemcpyAsync(ws.x_cur, state->x_cur, xb, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemcpyAsync(ws.x_best, state->x_best, xb, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemcpyAsync(ws.e_cur, state->e_cur, sb, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemcpyAsync(ws.e_best, state->e_best, sb, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemcpyAsync(ws.stepsize, state->stepsize, sb, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemcpyAsync(ws.win_accept, state->win_accept, ib, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemcpyAsync(ws.n_accept, state->n_accept, ib, cudaMemcpyDeviceToDevice, tu.s);
+        cudaMemsetAsync(tu.st, 0, sizeof(lj_stats), tu.s);
+        cudaEventRecord(tu.ev0, tu.s);
+        lj_status st = bh_step_batched(ctx, &ws, &pp, nullptr, tu.st, stream);
+        cudaEventRecord(tu.ev1, tu.s);
+        if (st != LJ_OK) return st;
+        if (cudaEventSynchronize(tu.ev1) != cudaSuccess)
+          return fail(ctx, LJ_ERR_CUDA, "autotune_bh: tuning run failed");
+        cudaEventElapsedTime(&ms, tu.ev0, tu.ev1);
+        lj_stats hs;
+        if (cudaMemcpy(&hs, tu.st, sizeof(lj_stats), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return fail(ctx, LJ_ERR_CUDA, "autotune_bh: reading statistics failed");
+        conv = hs.converged;
+      }
+      *r = ms > 0.f ? (double)conv / ms : 0.0;
+      return LJ_OK;
+    };
+    const double sg0 = p->min.switch_gtol > 0.0 ? p->min.switch_gtol : kDefaultSwitchGtol;
+    double best = -1.0;
+    // threads per candidate (the kernel's choices for up to 64 atoms)
+    const int teams[3] = {32, 64, 128};
+    const int nteam = n <= 64 ? 3 : 1;
+    for (int t = 0; t < nteam && rc == LJ_OK; ++t) {
+      const int team = n <= 64 ? teams[t] : 0;
+      double r = 0.0;
+      rc = rate(team, sg0, 0, &r);
+      if (rc == LJ_OK && r > best) { best = r; best_team = team; }
+    }
+    best_sg = mixed ? sg0 : 0.0;
+    if (mixed) {
+      for (int v = 0; v < 3 && rc == LJ_OK; ++v) {
+        if (kSgChoices[v] == sg0) continue;
+        double r = 0.0;
+        rc = rate(best_team, kSgChoices[v], 0, &r);
+        if (rc == LJ_OK && r > best) { best = r; best_sg = kSgChoices[v]; }
+      }
+    }
+    if (rc == LJ_OK) {                            // history in global memory
+      ljh::Plan pl;
+      cudaError_t e = mixed ? ljh::bh_plan_mixed(n, p->min.m, W, p->K, best_team, &pl, false)
+                            : ljh::bh_plan_fp64(n, p->min.m, W, p->K, best_team, &pl, false);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "autotune_bh plan");
+      if (rc == LJ_OK && pl.hist_on_chip) {
+        double r = 0.0;
+        rc = rate(best_team, best_sg, 1, &r);
+        if (rc == LJ_OK && r > best) { best = r; best_hist = 1; }
+      }
+    }
+  }
+  if (rc != LJ_OK) return rc;
+  ctx->bh_tune_team = best_team;
+  ctx->bh_tune_sg = best_sg;
+  ctx->bh_tune_hist = best_hist;
+  ctx->bh_tuned = true;
+  if (out) lj_ctx_get_tuning(ctx, LJ_TUNE_BH, out);
   return LJ_OK;
 }
 

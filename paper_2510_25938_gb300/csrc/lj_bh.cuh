@@ -84,7 +84,10 @@ __global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhA
   carve_team<T>(sp, n, true, a.hist_on_chip ? a.hist_slot_bytes : 0, pos, hbuf, hist, tm.red,
                 word);
   MinParams p = to_dev(a.p);
-  p.tiled = n > kTileMinN;             // hbuf: pair buffer up to 64 atoms, tiles above 256
+  // hbuf: pair buffer up to 64 atoms, tile accumulators above 256; with
+  // one-sided rows chosen above 256 atoms it holds no pairs and is withdrawn
+  p.tiled = n > kTileMinN && !a.p.df_one_sided;
+  if (n > kTileMinN && a.p.df_one_sided) hbuf = nullptr;
   if (!a.hist_on_chip)
     hist = static_cast<unsigned char*>(a.hist) + ((size_t)w * K + k) * a.hist_slot_bytes;
   const uint32_t wg = (uint32_t)(a.walker0 + w);
@@ -231,12 +234,13 @@ __global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhA
 }
 
 template <int T, int A, bool MIXED>
-cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out) {
+cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out, bool hist_global) {
   out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
   out->team = T;
   if (K <= LJ_MAX_K) {                // one cluster of K CTAs per walker
-    const bool on_chip = bhc_head_bytes<T>(n_atoms) +
-                         team_smem_bytes<T>(n_atoms, true, out->slot_bytes) <= kSmemBudget;
+    const bool on_chip = !hist_global && bhc_head_bytes<T>(n_atoms) +
+                                             team_smem_bytes<T>(n_atoms, true, out->slot_bytes) <=
+                                         kSmemBudget;
     out->hist_on_chip = on_chip ? 1 : 0;
     out->slots = on_chip ? 0 : (int64_t)n_walkers * K;
     const size_t smem = bhc_head_bytes<T>(n_atoms) +
@@ -297,9 +301,11 @@ cudaError_t dispatch_bh(int n, int team, F&& f) {
 }
 
 template <bool MIXED>
-cudaError_t plan_impl(int n_atoms, int m, int n_walkers, int K, int team, ljh::Plan* out) {
+cudaError_t plan_impl(int n_atoms, int m, int n_walkers, int K, int team, ljh::Plan* out,
+                      bool hist_global) {
   return dispatch_bh(n_atoms, team, [&](auto TT, auto AA) -> cudaError_t {
-    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(n_atoms, m, n_walkers, K, out);
+    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(n_atoms, m, n_walkers, K, out,
+                                                                     hist_global);
   });
 }
 

@@ -3,8 +3,9 @@
 
 namespace ljh {
 
-cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out) {
-  return ljbh::plan_impl<true>(n_atoms, m, n_walkers, K, team, out);
+cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out,
+                          bool hist_global) {
+  return ljbh::plan_impl<true>(n_atoms, m, n_walkers, K, team, out, hist_global);
 }
 
 cudaError_t bh_launch_mixed(const BhArgs& a, const Plan& plan, cudaStream_t s) {

@@ -17,6 +17,8 @@ struct MinParamsH {     // mirror of ljd::MinParams (plain data)
   long long deadline;
   LjConsts k;             // Eq. (1) constants from eps and sigma
   double f32_resolution, df_resolution;   // handover thresholds, relative to |E|
+  int df_one_sided = 0;   // double-float evaluations in one-sided rows even where
+                          // the team could use tiles (clusters above 256 atoms)
 };
 
 struct EvalArgs {
@@ -96,8 +98,12 @@ constexpr int kMaxAtoms = LJ_MAX_ATOMS;
 cudaError_t eval_launch(const EvalArgs& a, cudaStream_t s);
 // team: threads per candidate requested for clusters of up to 64 atoms
 // (32, 64 or 128); any other value picks the default for the cluster size.
-cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int team, Plan* out);
-cudaError_t lbfgs_plan_mixed(int max_n, int m, int64_t n_cand, int device, int team, Plan* out);
+// hist_global: keep the L-BFGS history in global memory even where it would
+// fit in shared memory (a tuning choice; results do not change)
+cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int team, Plan* out,
+                            bool hist_global = false);
+cudaError_t lbfgs_plan_mixed(int max_n, int m, int64_t n_cand, int device, int team, Plan* out,
+                             bool hist_global = false);
 cudaError_t lbfgs_launch_fp64(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
 cudaError_t lbfgs_launch_mixed(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
 // sort candidates of an uneven batch into size buckets (device, no sync)
@@ -106,8 +112,10 @@ cudaError_t bucketize_launch(const int64_t* off, int64_t n_cand, int nb, const B
 // autotuner inputs: n_cand uniform cube starts of n atoms, side `side` (device)
 cudaError_t tune_starts_launch(double* x, int64_t n_cand, int n, double side, uint64_t seed,
                                cudaStream_t s);
-cudaError_t bh_plan_fp64(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
-cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out);
+cudaError_t bh_plan_fp64(int n_atoms, int m, int n_walkers, int K, int team, Plan* out,
+                         bool hist_global = false);
+cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out,
+                          bool hist_global = false);
 cudaError_t bh_launch_fp64(const BhArgs& a, const Plan& plan, cudaStream_t s);
 cudaError_t bh_launch_mixed(const BhArgs& a, const Plan& plan, cudaStream_t s);
 

@@ -43,7 +43,12 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
   carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true, hb), a.max_n, true, hb, pos,
                 hbuf, hist, tm.red, word);
   MinParams p = to_dev(a.p);
-  p.tiled = a.max_n > kTileMinN;       // hbuf: pair buffer up to 64 atoms, tiles above 256
+  // hbuf: pair buffer up to 64 atoms, tile accumulators above 256.  With
+  // one-sided rows chosen above 256 atoms there is no pair buffer to use: the
+  // buffer holds 24 bytes per atom, not per pair, so it is withdrawn and every
+  // tier evaluates in one-sided rows
+  p.tiled = a.max_n > kTileMinN && !a.p.df_one_sided;
+  if (a.max_n > kTileMinN && a.p.df_one_sided) hbuf = nullptr;
   const long long slot = (long long)blockIdx.x * TPC + team;
   if (!a.hist_on_chip) hist = static_cast<unsigned char*>(a.hist) + slot * a.hist_slot_bytes;
 
@@ -130,11 +135,13 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
 }
 
 template <int T, int A, bool MIXED>
-cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out) {
+cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out,
+                     bool hist_global) {
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
   const size_t hist_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
-  const bool on_chip = TPC * team_smem_bytes<T>(max_n, true, hist_bytes) <= kSmemBudget;
+  const bool on_chip =
+      !hist_global && TPC * team_smem_bytes<T>(max_n, true, hist_bytes) <= kSmemBudget;
   const size_t smem = TPC * team_smem_bytes<T>(max_n, true, on_chip ? hist_bytes : 0);
   auto k = lbfgs_kernel<T, A, MIXED>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -204,9 +211,11 @@ cudaError_t dispatch_lb(int max_n, int team, F&& f) {
 }
 
 template <bool MIXED>
-cudaError_t plan_impl(int max_n, int m, int64_t n_cand, int device, int team, ljh::Plan* out) {
+cudaError_t plan_impl(int max_n, int m, int64_t n_cand, int device, int team, ljh::Plan* out,
+                      bool hist_global) {
   return dispatch_lb(max_n, team, [&](auto TT, auto AA) -> cudaError_t {
-    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(max_n, m, n_cand, device, out);
+    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(max_n, m, n_cand, device, out,
+                                                                     hist_global);
   });
 }
 

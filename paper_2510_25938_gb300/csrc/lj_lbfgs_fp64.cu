@@ -47,8 +47,9 @@ cudaError_t tune_starts_launch(double* x, int64_t n_cand, int n, double side, ui
   return cudaGetLastError();
 }
 
-cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int team, Plan* out) {
-  return ljlb::plan_impl<false>(max_n, m, n_cand, device, team, out);
+cudaError_t lbfgs_plan_fp64(int max_n, int m, int64_t n_cand, int device, int team, Plan* out,
+                            bool hist_global) {
+  return ljlb::plan_impl<false>(max_n, m, n_cand, device, team, out, hist_global);
 }
 
 cudaError_t lbfgs_launch_fp64(const LbfgsArgs& a, const Plan& plan, cudaStream_t s) {

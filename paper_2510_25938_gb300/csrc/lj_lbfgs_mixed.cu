@@ -3,8 +3,9 @@
 
 namespace ljh {
 
-cudaError_t lbfgs_plan_mixed(int max_n, int m, int64_t n_cand, int device, int team, Plan* out) {
-  return ljlb::plan_impl<true>(max_n, m, n_cand, device, team, out);
+cudaError_t lbfgs_plan_mixed(int max_n, int m, int64_t n_cand, int device, int team, Plan* out,
+                             bool hist_global) {
+  return ljlb::plan_impl<true>(max_n, m, n_cand, device, team, out, hist_global);
 }
 
 cudaError_t lbfgs_launch_mixed(const LbfgsArgs& a, const Plan& plan, cudaStream_t s) {

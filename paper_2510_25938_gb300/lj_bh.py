@@ -25,7 +25,9 @@ LJ_PREC_FP64, LJ_PREC_FP32, LJ_PREC_MIXED = 0, 1, 2
  LJ_CAND_TIMEOUT, LJ_CAND_BAD_INPUT) = range(6)
 LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 16
 LJ_OPT_BH_TEAM, LJ_OPT_LBFGS_TEAM, LJ_OPT_F32_HANDOVER, LJ_OPT_DF_HANDOVER = 1, 2, 3, 4
+LJ_OPT_HISTORY, LJ_OPT_DF_EVAL = 5, 6
 LJ_TUNE_BUCKETS = 6
+LJ_TUNE_BH = LJ_TUNE_BUCKETS
 STATS_FIELDS = ("evals32", "evals64", "evals_df", "iters32", "iters64", "pairs32", "pairs64",
                 "pairs_df", "vec_elems32", "vec_elems64", "converged", "minimisations",
                 "cycles32", "cycles_df", "cycles64", "cycles_direction", "cycles_linesearch")
@@ -54,6 +56,12 @@ class _Bh(C.Structure):
                 ("interval", C.c_int32), ("factor", C.c_double), ("seed", C.c_uint64),
                 ("step0", C.c_int64), ("n_steps", C.c_int32), ("walker0", C.c_int64),
                 ("min", _Lbfgs)]
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("team", C.c_int32), ("switch_gtol", C.c_double),
+                ("history_global", C.c_int32), ("df_one_sided", C.c_int32),
+                ("tuned", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -119,6 +127,11 @@ def load():
                                                   C.c_int64, C.POINTER(C.c_int32),
                                                   C.POINTER(C.c_double), P]
             lib.lj_ctx_autotune_batch.restype = C.c_int
+            lib.lj_ctx_get_tuning.argtypes = [P, C.c_int32, C.POINTER(_Tuning)]
+            lib.lj_ctx_get_tuning.restype = C.c_int
+            lib.lj_ctx_autotune_bh.argtypes = [P, C.POINTER(_State), C.POINTER(_Bh),
+                                               C.POINTER(_Tuning), P]
+            lib.lj_ctx_autotune_bh.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -190,6 +203,27 @@ class Ctx:
                                                   max_sample, C.byref(team), C.byref(sg),
                                                   _stream(stream)), "lj_ctx_autotune_batch")
         return {"team": team.value, "switch_gtol": sg.value}
+
+    def tuning(self, bucket: int) -> dict:
+        """lj_ctx_get_tuning: the tuning entry of a size bucket (0..5) or of
+        bh_step_batched (LJ_TUNE_BH)."""
+        t = _Tuning()
+        _check(self, load().lj_ctx_get_tuning(self.handle, bucket, C.byref(t)), "lj_ctx_get_tuning")
+        return {k: getattr(t, k) for k, _ in _Tuning._fields_}
+
+    def autotune_bh(self, state: dict, params: "BhParams", stream=None) -> dict:
+        """lj_ctx_autotune_bh on copies of the walker state (left unchanged):
+        team, switch_gtol and history placement for bh_step_batched."""
+        for k, dt in STATE_KEYS:
+            if state[k].dtype != dt:
+                raise ValueError(f"state[{k}] must be {dt}")
+        W, n3 = state["x_cur"].shape
+        s = _State(W, n3 // 3, *(_ptr(state[k]) for k, _ in STATE_KEYS))
+        t = _Tuning()
+        p = params.c()
+        _check(self, load().lj_ctx_autotune_bh(self.handle, C.byref(s), C.byref(p), C.byref(t),
+                                               _stream(stream)), "lj_ctx_autotune_bh")
+        return {k: getattr(t, k) for k, _ in _Tuning._fields_}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -62,3 +62,7 @@ def test_null_ctx_is_rejected(lib):
     lib.lbfgs_minimize_batched.restype = ctypes.c_int
     assert lib.lbfgs_minimize_batched(None, None, None, None, None, None, None, None, None,
                                       None) == -1
+    lib.lj_ctx_get_tuning.restype = ctypes.c_int
+    assert lib.lj_ctx_get_tuning(None, 0, None) == -1
+    lib.lj_ctx_autotune_bh.restype = ctypes.c_int
+    assert lib.lj_ctx_autotune_bh(None, None, None, None, None) == -1

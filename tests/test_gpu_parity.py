@@ -457,6 +457,99 @@ def test_autotune_batch_on_own_starts(lj):
     c.close()
 
 
+def test_autotune_records_every_dimension(lj):
+    """lj_ctx_autotune fills one tuning entry per bucket up to max_n (team,
+    switch_gtol, history placement, double-float evaluation form); the
+    table reads back through lj_ctx_get_tuning."""
+    c = lj.Ctx(0)
+    tuned = c.autotune(100, 10, lj.LJ_PREC_MIXED)
+    for b in range(lj.LJ_TUNE_BUCKETS):
+        t = c.tuning(b)
+        assert t["team"] == tuned["team"][b] and t["switch_gtol"] == tuned["switch_gtol"][b]
+        assert t["tuned"] == (1 if b < 3 else 0)
+        assert t["history_global"] in (0, 1) and t["df_one_sided"] == 0
+    assert c.tuning(lj.LJ_TUNE_BH)["tuned"] == 0
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_history_placement_does_not_change_results(lj, prec):
+    """LJ_OPT_HISTORY moves the L-BFGS history between shared and global
+    memory; the arithmetic is the same, so the minima are bit-identical."""
+    x0 = I.cube_starts(40, 38, 3.2, I.workload_seed(1) + 300)
+    out = []
+    for h in (2, 1):
+        c = lj.Ctx(0)
+        c.set_option(lj.LJ_OPT_HISTORY, h)
+        out.append(_minimise_gpu(lj, c, x0, uniform_n=38, prec=prec))
+        c.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    # and the BH kernel
+    res = []
+    for h in (2, 1):
+        c = lj.Ctx(0)
+        c.set_option(lj.LJ_OPT_HISTORY, h)
+        st = _bh_start(6, 38, 3.2, I.workload_seed(1) + 302)
+        gs = _gpu_state(lj, st)
+        tr = lj.new_trace(3, 6, 4)
+        lj.bh_step_batched(c, gs, lj.BhParams(K=4, kT=0.8, seed=3, n_steps=3,
+                                              min=lj.LbfgsParams(prec=prec)), tr)
+        res.append(tr["trial_e"].cpu().numpy())
+        c.close()
+    assert np.array_equal(res[0], res[1])
+
+
+def test_df_evaluation_forms_give_valid_minima(lj):
+    """LJ_OPT_DF_EVAL: 300-atom mixed minimisations with the double-float
+    polish in 32 x 32 tiles (each pair once) or in one-sided rows: every
+    minimum valid, and where both reach the same basin the energies agree."""
+    n_cand, n_atoms = 8, 300
+    x0 = I.fcc_fragments(n_cand, n_atoms, 0.1, I.workload_seed(4) + 300)
+    res = []
+    for form in (2, 1):
+        c = lj.Ctx(0)
+        c.set_option(lj.LJ_OPT_DF_EVAL, form)
+        xg, eg, sg, it, ne, stats = _minimise_gpu(lj, c, x0, uniform_n=n_atoms, prec=2, m=20)
+        c.close()
+        assert (sg == O.CONVERGED).all() and stats["evals_df"] > 0
+        for k in range(n_cand):
+            e_chk, g_chk = numpy_energy_grad(xg[3 * n_atoms * k:3 * n_atoms * (k + 1)])
+            assert np.abs(g_chk).max() < GTOL * 1.01 and abs(e_chk - eg[k]) <= 1e-9 * abs(eg[k])
+        res.append((xg.reshape(n_cand, -1), eg))
+    same = [k for k in range(n_cand) if same_basin(res[0][0][k], res[1][0][k])]
+    for k in same:
+        assert abs(res[0][1][k] - res[1][1][k]) <= MIX_ABS_FINAL
+    record("df_eval_forms_300", same_basin=len(same), candidates=n_cand)
+
+
+def test_autotune_bh_on_own_walkers(lj):
+    """lj_ctx_autotune_bh times team, switch_gtol and history placement on
+    copies of the caller's walkers (left unchanged); later steps with
+    switch_gtol = 0 use the choice and stay self-consistent."""
+    c = lj.Ctx(0)
+    st = _bh_start(16, 38, 3.2, I.workload_seed(1) + 400)
+    gs = _gpu_state(lj, st)
+    keep = {k: v.clone() for k, v in gs.items()}
+    p = lj.BhParams(K=4, kT=0.8, seed=9, n_steps=2, min=lj.LbfgsParams(prec=2))
+    t = c.autotune_bh(gs, p)
+    assert t["tuned"] == 1 and t["team"] in (32, 64, 128)
+    assert t["switch_gtol"] in (1e-3, 3e-4, 1e-4) and t["history_global"] in (0, 1)
+    assert c.tuning(lj.LJ_TUNE_BH) == t
+    for k in gs:
+        assert torch.equal(gs[k], keep[k]), k
+    p.n_steps = 3
+    tr = lj.new_trace(3, 16, 4)
+    lj.bh_step_batched(c, gs, p, tr)
+    torch.cuda.synchronize()
+    xb = gs["x_best"].cpu().numpy()
+    eb = gs["e_best"].cpu().numpy()
+    for w in range(16):
+        assert abs(numpy_energy_grad(xb[w])[0] - eb[w]) <= 1e-9 * abs(eb[w])
+    assert np.all(tr["trial_status"].cpu().numpy() != O.NONFINITE)
+    record("autotune_bh_lj38", **{k: v for k, v in t.items()})
+    c.close()
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 def test_minimise_bh_trial_moves_lj38(lj, ctx, prec):
     """Trial moves of the paper's kind (perturbations of minima by +-0.4
