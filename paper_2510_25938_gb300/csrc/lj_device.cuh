@@ -582,6 +582,13 @@ __device__ __forceinline__ int pair_index(int n, int i, int j) {
   return i * (2 * n - i - 1) / 2 + (j - i - 1);
 }
 
+// pair_index(n, a, b) = row_base(n, a) + b, so that pair (j, i), j < i, sits at
+// row_base(n, j) + i and pair (i, j), j > i, at row_base(n, i) + j;
+// row_base(n, j + 1) = row_base(n, j) + n - j - 2, row_base(n, 0) = -1
+__device__ __forceinline__ int row_base(int n, int i) {
+  return i * (2 * n - i - 1) / 2 - i - 1;
+}
+
 // first pair (i, j) of thread `rank` (p = rank); -1 if none
 __device__ __forceinline__ void pair_start(int n, int p, int& i, int& j) {
   i = 0;

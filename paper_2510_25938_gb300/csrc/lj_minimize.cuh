@@ -201,19 +201,26 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
         for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
           const int ii = q3 / 3;
           const ff* vc = vb + (q3 - 3 * ii) * np;
-          ff s0{0.f, 0.f}, s1{0.f, 0.f};
-          int q = ii - 1;                       // pair (0, ii)
-          for (int jj = 0; jj < ii; ++jj) {     // -v over j < i
-            const ff v = vc[q];
-            if (jj & 1) s1 = df_sub(s1, v); else s0 = df_sub(s0, v);
-            q += n - jj - 2;
+          // All lanes walk j = 0 .. n-1 together (no divergence), four
+          // independent sums, loads issued a block of four ahead of the adds.
+          const int ri = row_base(n, ii);
+          int rj = -1;                          // row_base(n, j)
+          ff s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+          for (int j0 = 0; j0 < n; j0 += 4) {
+            ff v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = j0 + u;
+              const int q = j < ii ? rj + ii : ri + j;
+              v[u] = ff{0.f, 0.f};
+              if (j < n && j != ii) v[u] = vc[q];
+              if (j < ii) v[u] = ff{-v[u].hi, -v[u].lo};   // -v over j < i
+              rj += n - j - 2;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[u] = df_add(s[u], v[u]);
           }
-          q = pair_index(n, ii, ii + 1);
-          for (int jj = ii + 1; jj < n; ++jj, ++q) {   // +v over j > i
-            const ff v = vc[q];
-            if (jj & 1) s1 = df_add(s1, v); else s0 = df_add(s0, v);
-          }
-          const ff sum = df_add(s0, s1);
+          const ff sum = df_add(df_add(s[0], s[1]), df_add(s[2], s[3]));
           gsum[q3] = -gs * (sum.hi + sum.lo);
         }
         tm.sync();
@@ -246,17 +253,24 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
         for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
           const int ii = q3 / 3;
           const double* vc = vb + (q3 - 3 * ii) * np;
-          double s0 = 0.0, s1 = 0.0;
-          int q = ii - 1;
-          for (int jj = 0; jj < ii; ++jj) {
-            if (jj & 1) s1 -= vc[q]; else s0 -= vc[q];
-            q += n - jj - 2;
+          const int ri = row_base(n, ii);       // same walk as the df sums
+          int rj = -1;
+          double s[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int j0 = 0; j0 < n; j0 += 4) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = j0 + u;
+              const int q = j < ii ? rj + ii : ri + j;
+              v[u] = 0.0;
+              if (j < n && j != ii) v[u] = vc[q];
+              if (j < ii) v[u] = -v[u];
+              rj += n - j - 2;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[u] += v[u];
           }
-          q = pair_index(n, ii, ii + 1);
-          for (int jj = ii + 1; jj < n; ++jj, ++q) {
-            if (jj & 1) s1 += vc[q]; else s0 += vc[q];
-          }
-          gsum[q3] = -gs * (s0 + s1);
+          gsum[q3] = -gs * ((s[0] + s[1]) + (s[2] + s[3]));
         }
         tm.sync();
         E = team_sum_dd<T>(tm, e) * p.k.e4;
