@@ -10,6 +10,9 @@ Every function states the passage of arXiv 2510.25938 it follows:
 
 * ``lj_energy_grad`` -- Methodology, "Lennard-Jones Potential", Eq. (1), and
   its analytic gradient.
+* ``morse_energy_grad`` -- the Morse pair potential (Morse 1929, cluster
+  form), the pair-potential extension the Conclusions point to; every batch
+  driver, the minimiser and ``bh_run`` take it as ``potential=OBJ_MORSE``.
 * ``lbfgs_minimize`` -- Methodology, "Algorithm Overview" step 2 and
   "Implementation Notes" (L-BFGS-B, read as unbounded L-BFGS with the
   two-loop recursion, a strong-Wolfe line search and the gradient inf-norm
@@ -36,7 +39,7 @@ _SO = os.path.join(_BUILD, "liblj_oracle.so")
 _SRC = [os.path.join(_HERE, "lj_oracle.c"), os.path.join(_HERE, "lj_oracle.h")]
 
 CONVERGED, MAXITER, LINESEARCH_FAIL, NONFINITE, TIMEOUT, BAD_INPUT = range(6)
-OBJ_LJ, OBJ_QUADRATIC, OBJ_ROSENBROCK, OBJ_POLY1D = range(4)
+OBJ_LJ, OBJ_QUADRATIC, OBJ_ROSENBROCK, OBJ_POLY1D, OBJ_MORSE = range(5)
 LS_FAILED, LS_WOLFE, LS_FALLBACK = range(3)
 LS_LOG_MAX = 64
 
@@ -67,7 +70,8 @@ class LbfgsParams(C.Structure):
 
 class Objective(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n", C.c_int64), ("A", C.c_void_p),
-                ("b", C.c_void_p), ("eps", C.c_double), ("sigma", C.c_double)]
+                ("b", C.c_void_p), ("eps", C.c_double), ("sigma", C.c_double),
+                ("rho", C.c_double)]
 
 
 class LsLog(C.Structure):
@@ -86,7 +90,8 @@ class BhParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("kT", C.c_double), ("target_rate", C.c_double),
                 ("interval", C.c_int32), ("factor", C.c_double), ("seed", C.c_uint64),
                 ("step0", C.c_int64), ("n_steps", C.c_int32), ("walker0", C.c_int64),
-                ("eps", C.c_double), ("sigma", C.c_double), ("min", LbfgsParams)]
+                ("eps", C.c_double), ("sigma", C.c_double), ("min", LbfgsParams),
+                ("potential", C.c_int32), ("rho", C.c_double)]
 
 
 def _load():
@@ -104,6 +109,9 @@ def _load():
             lib.orc_stream_uniform.restype = C.c_double
             lib.orc_lj_energy_grad.argtypes = [C.c_int64, P, P, C.c_double, C.c_double]
             lib.orc_lj_energy_grad.restype = C.c_double
+            lib.orc_morse_energy_grad.argtypes = [C.c_int64, P, P, C.c_double, C.c_double,
+                                                  C.c_double]
+            lib.orc_morse_energy_grad.restype = C.c_double
             lib.orc_lbfgs_direction.argtypes = [C.c_int64, C.c_int32, P, P, P, P, P]
             lib.orc_lbfgs_direction.restype = None
             lib.orc_cubic_interpolate.argtypes = [C.c_double] * 6
@@ -136,6 +144,13 @@ def _load():
                                             C.POINTER(LbfgsParams), C.c_double, C.c_double,
                                             P, P, P, P, C.c_int32]
             lib.orc_lbfgs_batch.restype = None
+            lib.orc_eval_batch_pot.argtypes = [C.c_int64, C.c_int32, P, P, P, P, C.c_int32,
+                                               C.c_double, C.c_double, C.c_double, C.c_int32]
+            lib.orc_eval_batch_pot.restype = None
+            lib.orc_lbfgs_batch_pot.argtypes = [C.c_int64, C.c_int32, P, P,
+                                                C.POINTER(LbfgsParams), C.c_int32, C.c_double,
+                                                C.c_double, C.c_double, P, P, P, P, C.c_int32]
+            lib.orc_lbfgs_batch_pot.restype = None
             lib.orc_bh_run.argtypes = [C.c_int64, C.c_int32, P, P, P, P, P, P, P,
                                        C.POINTER(BhParams), P, P, P, P, P, C.c_int32]
             lib.orc_bh_run.restype = None
@@ -199,6 +214,15 @@ def lj_energy_grad(x, eps: float = 1.0, sigma: float = 1.0):
     return float(e), g
 
 
+def morse_energy_grad(x, eps: float = 1.0, re: float = 1.0, rho: float = 6.0):
+    """Morse energy eps sum_{i<j} e_ij (e_ij - 2), e_ij = exp(rho (1 - r_ij / re)),
+    and its gradient for one cluster; x is (N,3) or flat 3N."""
+    x = _f64(x).reshape(-1)
+    g = np.zeros_like(x)
+    e = _load().orc_morse_energy_grad(x.size // 3, _ptr(x), _ptr(g), eps, re, rho)
+    return float(e), g
+
+
 def lbfgs_direction(S, Y, g) -> np.ndarray:
     """Two-loop recursion: d = -H g for history rows S, Y (oldest first)."""
     S = _f64(S)
@@ -216,14 +240,15 @@ def cubic_interpolate(a, fa, ga, b, fb, gb) -> float:
 
 
 def minimize(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None, b=None,
-             eps: float = 1.0, sigma: float = 1.0):
-    """Minimise one objective from x0.  Returns (x, f, status, iters, nevals)."""
+             eps: float = 1.0, sigma: float = 1.0, rho: float = 6.0):
+    """Minimise one objective from x0 (OBJ_MORSE: eps, sigma = re, rho).
+    Returns (x, f, status, iters, nevals)."""
     p = params or MinParams()
     x = _f64(x0).reshape(-1).copy()
     n = x.size
     Aa = _f64(A) if A is not None else None
     ba = _f64(b) if b is not None else None
-    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma)
+    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma, rho)
     work = np.zeros((4 + 2 * p.m) * n + p.m + 1)
     f = C.c_double()
     it = C.c_int32()
@@ -235,7 +260,8 @@ def minimize(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None, b=
 
 
 def minimize_log(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None, b=None,
-                 eps: float = 1.0, sigma: float = 1.0, max_steps: int = 20000):
+                 eps: float = 1.0, sigma: float = 1.0, max_steps: int = 20000,
+                 rho: float = 6.0):
     """minimize() that also returns a record of every accepted step: a
     structured array with alpha, f0, f, dphi0, dphi (phi'(alpha) along the
     step's direction), exit (LS_WOLFE / LS_FALLBACK), retried, n_trial."""
@@ -244,7 +270,7 @@ def minimize_log(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None
     n = x.size
     Aa = _f64(A) if A is not None else None
     ba = _f64(b) if b is not None else None
-    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma)
+    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma, rho)
     work = np.zeros((4 + 2 * p.m) * n + p.m + 1)
     logs = (StepLog * max_steps)()
     f = C.c_double()
@@ -260,7 +286,7 @@ def minimize_log(x0, kind: int = OBJ_LJ, params: MinParams | None = None, A=None
 
 
 def line_search(x, d, alpha1: float, kind: int = OBJ_POLY1D, params: MinParams | None = None,
-                A=None, b=None, eps: float = 1.0, sigma: float = 1.0):
+                A=None, b=None, eps: float = 1.0, sigma: float = 1.0, rho: float = 6.0):
     """One strong-Wolfe line search of the oracle from x along d with first
     trial alpha1.  Returns a dict: ok, alpha, f (accepted point), f0, dphi0,
     trials (k x 3 array of alpha, phi, phi' in evaluation order; a final
@@ -272,7 +298,7 @@ def line_search(x, d, alpha1: float, kind: int = OBJ_POLY1D, params: MinParams |
     n = x.size
     Aa = _f64(A) if A is not None else None
     ba = _f64(b) if b is not None else None
-    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma)
+    obj = Objective(kind, n, _ptr(Aa), _ptr(ba), eps, sigma, rho)
     work = np.zeros(3 * n)
     log = LsLog()
     a = C.c_double()
@@ -295,20 +321,24 @@ def _layout(n_cand, uniform_n, atom_off):
 
 
 def eval_batch(x, n_cand: int, uniform_n: int = 0, atom_off=None, eps=1.0, sigma=1.0,
-               grad: bool = True, n_threads: int = 0):
-    """Energy (and gradient) of a batch of clusters with packed xyz coordinates."""
+               grad: bool = True, n_threads: int = 0, potential: int = OBJ_LJ,
+               rho: float = 6.0):
+    """Energy (and gradient) of a batch of clusters with packed xyz coordinates
+    (potential OBJ_LJ, or OBJ_MORSE with sigma = re and range rho)."""
     un, off = _layout(n_cand, uniform_n, atom_off)
     x = _f64(x).reshape(-1)
     e = np.zeros(n_cand)
     g = np.zeros_like(x) if grad else None
-    _load().orc_eval_batch(n_cand, un, _ptr(off), _ptr(x), _ptr(e), _ptr(g), eps, sigma,
-                           n_threads)
+    _load().orc_eval_batch_pot(n_cand, un, _ptr(off), _ptr(x), _ptr(e), _ptr(g), potential,
+                               eps, sigma, rho, n_threads)
     return e, g
 
 
 def lbfgs_batch(x, n_cand: int, uniform_n: int = 0, atom_off=None,
-                params: MinParams | None = None, eps=1.0, sigma=1.0, n_threads: int = 0):
-    """Minimise a batch of LJ clusters in place (a copy is returned)."""
+                params: MinParams | None = None, eps=1.0, sigma=1.0, n_threads: int = 0,
+                potential: int = OBJ_LJ, rho: float = 6.0):
+    """Minimise a batch of clusters (LJ, or Morse with potential=OBJ_MORSE)
+    in place (a copy is returned)."""
     p = params or MinParams()
     un, off = _layout(n_cand, uniform_n, atom_off)
     x = _f64(x).reshape(-1).copy()
@@ -317,8 +347,8 @@ def lbfgs_batch(x, n_cand: int, uniform_n: int = 0, atom_off=None,
     it = np.zeros(n_cand, dtype=np.int32)
     ne = np.zeros(n_cand, dtype=np.int32)
     pc = p.c()
-    _load().orc_lbfgs_batch(n_cand, un, _ptr(off), _ptr(x), C.byref(pc), eps, sigma,
-                            _ptr(e), _ptr(st), _ptr(it), _ptr(ne), n_threads)
+    _load().orc_lbfgs_batch_pot(n_cand, un, _ptr(off), _ptr(x), C.byref(pc), potential, eps,
+                                sigma, rho, _ptr(e), _ptr(st), _ptr(it), _ptr(ne), n_threads)
     return x, e, st, it, ne
 
 
@@ -352,12 +382,14 @@ class BhParamsPy:
     eps: float = 1.0
     sigma: float = 1.0
     min: MinParams = None
+    potential: int = OBJ_LJ     # or OBJ_MORSE (sigma = re)
+    rho: float = 6.0
 
     def c(self) -> BhParams:
         mp = (self.min or MinParams()).c()
         return BhParams(self.K, self.kT, self.target_rate, self.interval, self.factor,
                         self.seed, self.step0, self.n_steps, self.walker0, self.eps,
-                        self.sigma, mp)
+                        self.sigma, mp, self.potential, self.rho)
 
 
 def bh_run(state: dict, params: BhParamsPy, n_threads: int = 0, trace: bool = True):

@@ -15,6 +15,11 @@
  * Algorithm for Lennard-Jones Clusters", arXiv 2510.25938):
  *   - LJ energy: Methodology, "Lennard-Jones Potential", Eq. (1); the gradient
  *     is the analytic derivative of Eq. (1) (the paper never writes it).
+ *   - Morse energy (Morse 1929, cluster form): the pair-potential extension
+ *     the Conclusions point to ("empirical force fields"); pinned in
+ *     tests/test_oracle_morse.py by its depth, zero crossing, harmonic
+ *     constant, closed-form small clusters, the icosahedral breathing
+ *     minimum, finite differences, invariants and the scaling law.
  *   - Local minimiser: Methodology, "Algorithm Overview" step 2 and
  *     "Implementation Notes" (L-BFGS-B from scipy, unbounded).  Read here as
  *     L-BFGS with the two-loop recursion (Nocedal & Wright, Numerical
@@ -160,14 +165,69 @@ double orc_lj_energy_grad(int64_t n_atoms, const double* x, double* g,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Objectives the minimiser can run on (LJ is the method; the quadratic and  */
-/* Rosenbrock functions exist only to pin the minimiser).                   */
+/* Morse pair potential (P. M. Morse, Phys. Rev. 34, 57 (1929)) in the form   */
+/* used for atomic clusters: V(r) = eps e^{rho(1 - r/re)} (e^{rho(1 - r/re)}  */
+/* - 2), depth eps at r = re, range set by rho.  It is an empirical pair      */
+/* potential of the kind the paper's Conclusions name as the next use of the  */
+/* method: the minimiser and Basin Hopping run on it unchanged.  Gradient:    */
+/* dV/dr = -(2 eps rho / re) e (e - 1), e = e^{rho(1 - r/re)}, and            */
+/* dE/dx_i = sum_j (dV/dr)(r_ij) (x_i - x_j) / r_ij.                          */
+/* ------------------------------------------------------------------------- */
+double orc_morse_energy_grad(int64_t n_atoms, const double* x, double* g,
+                             double eps, double re, double rho)
+{
+    double energy = 0.0, comp = 0.0;
+    if (g) {
+        for (int64_t c = 0; c < 3 * n_atoms; ++c) g[c] = 0.0;
+    }
+    for (int64_t i = 0; i < n_atoms; ++i) {
+        for (int64_t j = i + 1; j < n_atoms; ++j) {
+            double dx = x[3 * i + 0] - x[3 * j + 0];
+            double dy = x[3 * i + 1] - x[3 * j + 1];
+            double dz = x[3 * i + 2] - x[3 * j + 2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0) {
+                /* coincident atoms: V is finite there but its gradient has no
+                 * direction; treated as an invalid configuration, as for LJ */
+                if (g) {
+                    for (int64_t c = 0; c < 3 * n_atoms; ++c) g[c] = NAN;
+                }
+                return INFINITY;
+            }
+            double r = sqrt(r2);
+            double e = exp(rho * (1.0 - r / re));
+            double term = eps * e * (e - 2.0);
+            double t = energy + term;          /* Neumaier-compensated sum */
+            if (fabs(energy) >= fabs(term)) comp += (energy - t) + term;
+            else comp += (term - t) + energy;
+            energy = t;
+            if (g) {
+                double c = -2.0 * eps * rho / re * e * (e - 1.0) / r;   /* (dV/dr) / r */
+                g[3 * i + 0] += c * dx;
+                g[3 * i + 1] += c * dy;
+                g[3 * i + 2] += c * dz;
+                g[3 * j + 0] -= c * dx;
+                g[3 * j + 1] -= c * dy;
+                g[3 * j + 2] -= c * dz;
+            }
+        }
+    }
+    return energy + comp;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Objectives the minimiser can run on (LJ is the method, Morse its pair-   */
+/* potential extension; the quadratic, Rosenbrock and one-dimensional        */
+/* polynomial functions exist only to pin the minimiser).                   */
 /* ------------------------------------------------------------------------- */
 static double orc_objective_eval(const orc_objective* o, const double* x, double* g)
 {
     int64_t n = o->n;
     if (o->kind == ORC_OBJ_LJ) {
         return orc_lj_energy_grad(n / 3, x, g, o->eps, o->sigma);
+    }
+    if (o->kind == ORC_OBJ_MORSE) {
+        return orc_morse_energy_grad(n / 3, x, g, o->eps, o->sigma, o->rho);
     }
     if (o->kind == ORC_OBJ_QUADRATIC) {
         /* f = 1/2 x^T A x - b^T x, g = A x - b (A symmetric, row-major) */
@@ -662,7 +722,8 @@ typedef struct {
     double* x;
     double* energy;
     double* grad;
-    double eps, sigma;
+    int32_t kind;            /* ORC_OBJ_LJ or ORC_OBJ_MORSE */
+    double eps, sigma, rho;
     const orc_lbfgs_params* p;
     int32_t* status;
     int32_t* iters;
@@ -686,13 +747,16 @@ static void orc_eval_item(void* vctx, int64_t c, double* work)
     orc_batch_ctx* b = (orc_batch_ctx*)vctx;
     int64_t a0, na;
     orc_cand_range(b, c, &a0, &na);
-    b->energy[c] = orc_lj_energy_grad(na, b->x_in + 3 * a0, b->grad ? b->grad + 3 * a0 : NULL,
-                                      b->eps, b->sigma);
+    double* gc = b->grad ? b->grad + 3 * a0 : NULL;
+    if (b->kind == ORC_OBJ_MORSE)
+        b->energy[c] = orc_morse_energy_grad(na, b->x_in + 3 * a0, gc, b->eps, b->sigma, b->rho);
+    else
+        b->energy[c] = orc_lj_energy_grad(na, b->x_in + 3 * a0, gc, b->eps, b->sigma);
 }
 
-void orc_eval_batch(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
-                    const double* x, double* energy, double* grad,
-                    double eps, double sigma, int32_t n_threads)
+void orc_eval_batch_pot(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
+                        const double* x, double* energy, double* grad, int32_t kind,
+                        double eps, double sigma, double rho, int32_t n_threads)
 {
     orc_batch_ctx b;
     memset(&b, 0, sizeof(b));
@@ -701,9 +765,19 @@ void orc_eval_batch(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
     b.x_in = x;
     b.energy = energy;
     b.grad = grad;
+    b.kind = kind;
     b.eps = eps;
     b.sigma = sigma;
+    b.rho = rho;
     orc_parallel_for(n_cand, n_threads, 0, orc_eval_item, &b);
+}
+
+void orc_eval_batch(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
+                    const double* x, double* energy, double* grad,
+                    double eps, double sigma, int32_t n_threads)
+{
+    orc_eval_batch_pot(n_cand, uniform_n, atom_off, x, energy, grad, ORC_OBJ_LJ, eps, sigma,
+                       0.0, n_threads);
 }
 
 static int64_t orc_max_atoms(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off)
@@ -724,10 +798,11 @@ static void orc_lbfgs_item(void* vctx, int64_t c, double* work)
     orc_cand_range(b, c, &a0, &na);
     orc_objective o;
     memset(&o, 0, sizeof(o));
-    o.kind = ORC_OBJ_LJ;
+    o.kind = b->kind;
     o.n = 3 * na;
     o.eps = b->eps;
     o.sigma = b->sigma;
+    o.rho = b->rho;
     double f;
     int32_t it, ne;
     int32_t st = orc_lbfgs_minimize(&o, b->x + 3 * a0, b->p, &f, &it, &ne, work);
@@ -742,14 +817,25 @@ void orc_lbfgs_batch(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
                      double* energy, int32_t* status, int32_t* iters, int32_t* nevals,
                      int32_t n_threads)
 {
+    orc_lbfgs_batch_pot(n_cand, uniform_n, atom_off, x, p, ORC_OBJ_LJ, eps, sigma, 0.0,
+                        energy, status, iters, nevals, n_threads);
+}
+
+void orc_lbfgs_batch_pot(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
+                         double* x, const orc_lbfgs_params* p, int32_t kind, double eps,
+                         double sigma, double rho, double* energy, int32_t* status,
+                         int32_t* iters, int32_t* nevals, int32_t n_threads)
+{
     orc_batch_ctx b;
     memset(&b, 0, sizeof(b));
     b.uniform_n = uniform_n;
     b.atom_off = atom_off;
     b.x = x;
     b.energy = energy;
+    b.kind = kind;
     b.eps = eps;
     b.sigma = sigma;
+    b.rho = rho;
     b.p = p;
     b.status = status;
     b.iters = iters;
@@ -794,10 +880,11 @@ static void orc_bh_item(void* vctx, int64_t wi, double* work)
     const uint32_t w = (uint32_t)(bp->walker0 + wi);
     orc_objective o;
     memset(&o, 0, sizeof(o));
-    o.kind = ORC_OBJ_LJ;
+    o.kind = bp->potential == ORC_OBJ_MORSE ? ORC_OBJ_MORSE : ORC_OBJ_LJ;
     o.n = n;
     o.eps = bp->eps;
     o.sigma = bp->sigma;
+    o.rho = bp->rho;
 
     for (int32_t i = 0; i < bp->n_steps; ++i) {
         const int64_t s64 = bp->step0 + i;

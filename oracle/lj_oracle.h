@@ -15,7 +15,8 @@ extern "C" {
 enum { ORC_CONVERGED = 0, ORC_MAXITER = 1, ORC_LINESEARCH_FAIL = 2, ORC_NONFINITE = 3,
        ORC_TIMEOUT = 4, ORC_BAD_INPUT = 5 };
 
-enum { ORC_OBJ_LJ = 0, ORC_OBJ_QUADRATIC = 1, ORC_OBJ_ROSENBROCK = 2, ORC_OBJ_POLY1D = 3 };
+enum { ORC_OBJ_LJ = 0, ORC_OBJ_QUADRATIC = 1, ORC_OBJ_ROSENBROCK = 2, ORC_OBJ_POLY1D = 3,
+       ORC_OBJ_MORSE = 4 };
 
 typedef struct {
     int32_t kind;          /* ORC_OBJ_* */
@@ -23,7 +24,8 @@ typedef struct {
     const double* A;       /* quadratic: n x n symmetric, row-major;
                               POLY1D: NULL, or A[0] = bound above which f = +inf */
     const double* b;       /* quadratic: n; POLY1D: 5 coefficients c0..c4 */
-    double eps, sigma;     /* LJ only */
+    double eps, sigma;     /* LJ: eps, sigma; Morse: eps, re */
+    double rho;            /* Morse range parameter */
 } orc_objective;
 
 typedef struct {
@@ -47,6 +49,8 @@ typedef struct {
     int64_t walker0;       /* global index of walker 0 of this call */
     double eps, sigma;
     orc_lbfgs_params min;
+    int32_t potential;     /* ORC_OBJ_LJ (0) or ORC_OBJ_MORSE (sigma = re) */
+    double rho;            /* Morse range parameter */
 } orc_bh_params;
 
 /* record of one line search (tests only) */
@@ -75,6 +79,8 @@ double orc_stream_uniform(uint64_t seed, uint32_t tag, uint32_t draw,
 
 double orc_lj_energy_grad(int64_t n_atoms, const double* x, double* g,
                           double eps, double sigma);
+double orc_morse_energy_grad(int64_t n_atoms, const double* x, double* g,
+                             double eps, double re, double rho);
 void orc_lbfgs_direction(int64_t n, int32_t cnt, const double* S, const double* Y,
                          const double* g, double* d, double* alpha_work);
 double orc_cubic_interpolate(double a, double fa, double ga, double b, double fb, double gb);
@@ -104,6 +110,15 @@ void orc_lbfgs_batch(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
                      double* x, const orc_lbfgs_params* p, double eps, double sigma,
                      double* energy, int32_t* status, int32_t* iters, int32_t* nevals,
                      int32_t n_threads);
+/* the same drivers for a chosen pair potential: kind ORC_OBJ_LJ or
+ * ORC_OBJ_MORSE (sigma = re, rho its range) */
+void orc_eval_batch_pot(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
+                        const double* x, double* energy, double* grad, int32_t kind,
+                        double eps, double sigma, double rho, int32_t n_threads);
+void orc_lbfgs_batch_pot(int64_t n_cand, int32_t uniform_n, const int64_t* atom_off,
+                         double* x, const orc_lbfgs_params* p, int32_t kind, double eps,
+                         double sigma, double rho, double* energy, int32_t* status,
+                         int32_t* iters, int32_t* nevals, int32_t n_threads);
 void orc_bh_run(int64_t n_walkers, int32_t n_atoms, double* x_cur, double* e_cur,
                 double* x_best, double* e_best, double* stepsize, int32_t* win_accept,
                 int32_t* n_accept, const orc_bh_params* bp,
