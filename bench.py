@@ -33,8 +33,10 @@ The same JSON line also carries (one GPU only):
                     octahedron over the workload's 500 BH steps (mixed and,
                     as search_quality_fp64, the FP64 path);
   other_workloads   the sequential LJ13 walker, the uneven 4,096-candidate batch
-                    (one CUDA-graph replay) and the 500- and 1000-atom batches,
-                    mixed and FP64, each with an oracle sample on the host cores.
+                    (one CUDA-graph replay), the 500- and 1000-atom batches and
+                    the same Basin Hopping workload on the Morse potential
+                    (rho = 6), mixed and FP64, each with an oracle sample on the
+                    host cores.
 """
 from __future__ import annotations
 
@@ -84,10 +86,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true", help="skip the evaluation microbench")
     ap.add_argument("--workload", default="lj38-bh",
-                    choices=["lj38-bh", "uneven-4096", "large-500", "large-1000", "lj13-seq"],
+                    choices=["lj38-bh", "uneven-4096", "large-500", "large-1000", "lj13-seq",
+                             "morse38-bh"],
                     help="lj38-bh (default): the Basin Hopping step this bench reports; the "
                          "others time the batched minimisation of the uneven and large-cluster "
-                         "workloads, or one sequential FP64 LJ13 walker, and print their own line")
+                         "workloads, one sequential FP64 LJ13 walker, or the Basin Hopping "
+                         "workload on the Morse potential, and print their own line")
     ap.add_argument("--micro-only", action="store_true",
                     help="run only the evaluation microbench and print its JSON")
     ap.add_argument("--micro-repeats", type=int, default=100)
@@ -614,6 +618,121 @@ def run_sequential_lj13(args):
     return 0
 
 
+# Morse pair potential (the pair-potential extension of the method): the
+# headline's Basin Hopping workload with Eq. (1) replaced by Morse, rho = 6
+MORSE_RHO = 6.0
+# algorithmic flops of one Morse pair (difference 3, r^2 5, r 1, exponent 2,
+# exp 1, e(e-2) 2, e(e-1)/r 3, three gradient products and sums 6, energy
+# sum 1, counting the square root and the exponential as one each)
+MORSE_PAIR_FLOPS = 24.0
+
+
+def morse_bh_record(L, flush, reps, warmup, cpu_budget):
+    """Morse clusters of 38 atoms (rho = 6), 64 walkers x K = 8, 10 BH steps
+    per launch, cube starts side 3.2 re, kT = 0.8: converged minimisations per
+    second, mixed and FP64, with the oracle's Morse on the host cores."""
+    import torch
+    from paper_2510_25938_gb300 import inputs as I
+    import oracle as O
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seed = I.workload_seed(CONFIG_ID) + 770
+    x0 = I.cube_starts(WALKERS, N_ATOMS, SIDE, seed)
+    ctx = L.Ctx()
+    ctx.reserve(WALKERS * K, N_ATOMS, 10)
+    xs = torch.as_tensor(x0.reshape(-1), dtype=torch.float64, device=dev).contiguous()
+    es = torch.empty(WALKERS, dtype=torch.float64, device=dev)
+    L.lbfgs_minimize_batched(ctx, xs, es, n_cand=WALKERS, uniform_n=N_ATOMS,
+                             params=L.LbfgsParams(prec=L.LJ_PREC_FP64, potential=L.LJ_POT_MORSE,
+                                                  rho=MORSE_RHO))
+    xm = xs.view(WALKERS, -1)
+
+    def state():
+        return {"x_cur": xm.clone(), "e_cur": es.clone(), "x_best": xm.clone(),
+                "e_best": es.clone(),
+                "stepsize": torch.full((WALKERS,), STEP0, dtype=torch.float64, device=dev),
+                "win_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev),
+                "n_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev)}
+    out = {"workload": "Morse rho=6, N=38: 64 walkers x K=8, 10 BH steps per launch, cube "
+                       "starts side 3.2 re, kT=0.8, m=10, ||g||_inf<1e-6"}
+    for prec, pname in ((L.LJ_PREC_MIXED, "mixed"), (L.LJ_PREC_FP64, "fp64")):
+        p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH,
+                       min=L.LbfgsParams(prec=prec, switch_gtol=SWITCH_GTOL,
+                                         potential=L.LJ_POT_MORSE, rho=MORSE_RHO))
+        st = state()
+        stats = L.new_stats(dev)
+        times = []
+        n_rep = reps if pname == "mixed" else max(1, reps // 2)
+        for r in range(max(warmup, 1) + n_rep):
+            p.step0 = r * BH_PER_LAUNCH
+            if r == max(warmup, 1):
+                stats.zero_()
+            flush.fill_(float(r))
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            L.bh_step_batched(ctx, st, p, None, stats)
+            ev1.record()
+            torch.cuda.synchronize()
+            if r >= max(warmup, 1):
+                times.append(ev0.elapsed_time(ev1) / 1e3)
+        t = sum(times)
+        sd = L.stats_dict(stats)
+        fl = MORSE_PAIR_FLOPS * (sd["pairs32"] + sd["pairs64"]) + 8.0 * (
+            sd["vec_elems32"] + sd["vec_elems64"]) + 12.0 * 3 * N_ATOMS * (
+            sd["iters32"] + sd["iters64"])
+        out[pname] = {"value": sd["converged"] / t, "unit": "converged minimisations/s",
+                      "ms_per_launch": 1e3 * t / len(times), "launches": len(times),
+                      "converged_fraction": sd["converged"] / max(sd["minimisations"], 1),
+                      "achieved_tflops": fl / t / 1e12,
+                      "fp64_pair_share": sd["pairs64"] / max(sd["pairs32"] + sd["pairs64"], 1),
+                      "per_minimisation": {k: sd[k] / max(sd["minimisations"], 1) for k in (
+                          "evals32", "evals64", "iters32", "iters64")}}
+    ctx.close()
+    out["value"] = out["mixed"]["value"]
+    out["mixed_over_fp64"] = out["mixed"]["value"] / max(out["fp64"]["value"], 1e-30)
+    out["roofline"] = {"bound": "alu", "achieved": out["mixed"]["achieved_tflops"],
+                       "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": out["mixed"]["achieved_tflops"] / FP32_PEAK_TFLOPS,
+                       "kernel": "bh_cluster_kernel<64,1,mixed,Morse>",
+                       "flops": f"{MORSE_PAIR_FLOPS:g} per pair per evaluation + 8 per history "
+                                "element + 36 N per iteration"}
+    if cpu_budget > 0:
+        em = es.cpu().numpy()
+        ost = bh_state_np(xm.cpu().numpy(), em)
+        conv = steps = 0
+        t0 = time.perf_counter()
+        while steps == 0 or time.perf_counter() - t0 < cpu_budget:
+            tr = O.bh_run(ost, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=steps, n_steps=1,
+                                            potential=O.OBJ_MORSE, rho=MORSE_RHO))
+            conv += int((tr["trial_status"] == O.CONVERGED).sum())
+            steps += 1
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": conv / dt, "unit": "converged minimisations/s",
+                               "cores": O.num_threads(), "kind": "oracle",
+                               "sample": f"{steps} FP64 BH steps x 64 walkers x K=8 of Morse38 "
+                                         f"({conv} converged) in {dt:.1f} s"}
+    return out
+
+
+def run_morse(args):
+    import torch
+    from paper_2510_25938_gb300 import build as B
+    B.build()
+    from paper_2510_25938_gb300 import lj_bh as L
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rec = morse_bh_record(L, flush, args.steps, args.warmup,
+                          0.0 if args.no_cpu_baseline else 10.0)
+    line = {"metric": "converged Morse minimisations/s", "value": rec["value"],
+            "unit": "converged minimisations/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": rec["workload"], "precision": "mixed",
+                                            "l2": "flushed (256 MiB write) before each launch"}}
+    line.update({k: v for k, v in rec.items() if k not in ("workload", "value")})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # LJ38 global minimum: the fcc truncated octahedron (O_h), the structure the
 # paper's Results name, minimised by the oracle (stored fixture)
 def lj38_global_minimum_energy():
@@ -844,6 +963,7 @@ def run_cuda(args):
         others = {"lj13-seq": sequential_lj13_record(L, 3, 1)}
         for name in BATCH_WORKLOADS:
             others[name] = batch_workload_record(L, name, flush, 3, 1, cpu_b)
+        others["morse38-bh"] = morse_bh_record(L, flush, 3, 1, cpu_b)
         line["other_workloads"] = others
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(x0, seed)
@@ -973,6 +1093,8 @@ def main():
         return run_batch_workload(args)
     if args.workload == "lj13-seq":
         return run_sequential_lj13(args)
+    if args.workload == "morse38-bh":
+        return run_morse(args)
     return run_cuda(args)
 
 

@@ -19,6 +19,10 @@
  *                              best-of-K selection, Metropolis test, step-size
  *                              adaptation ("Algorithm Overview" steps 1-5).
  *
+ * Besides Eq. (1), every entry point runs on the Morse pair potential
+ * (lj_potential), the kind of empirical force field the paper's Conclusions
+ * name as the method's next use: the minimiser and Basin Hopping are the same.
+ *
  * Conventions for every call:
  *   - Coordinates are packed xyz per atom, atoms of a candidate contiguous,
  *     candidates contiguous: the flattened 3N vector of the paper
@@ -62,6 +66,16 @@ typedef enum {
 } lj_status;
 
 typedef enum { LJ_F32 = 0, LJ_F64 = 1 } lj_dtype;
+
+/* Pair potential of every energy the library computes.
+ *   LJ_POT_LJ     Eq. (1): E = 4 eps sum_{i<j} [(sigma/r)^12 - (sigma/r)^6].
+ *   LJ_POT_MORSE  Morse (Morse 1929, the form used for clusters):
+ *                 E = eps sum_{i<j} e_ij (e_ij - 2), e_ij = exp(rho (1 - r_ij / re)),
+ *                 with re passed in the sigma slot and rho > 0 its range
+ *                 (rho = 6 has the width of the LJ well).  Coincident atoms give a
+ *                 non-finite energy, as for Eq. (1).  The MIXED minimiser runs its
+ *                 FP32 tier and then FP64 (no double-float tier for this potential). */
+typedef enum { LJ_POT_LJ = 0, LJ_POT_MORSE = 1 } lj_potential;
 
 typedef enum {
     LJ_PREC_FP64 = 0,   /* every operation in FP64 */
@@ -116,7 +130,9 @@ typedef struct {
                                 costs up to 2000 FP32 iterations per minimisation) */
     int64_t deadline_cycles; /* > 0: a candidate still running after this many
                                 SM clock cycles stops with LJ_CAND_TIMEOUT */
-    double eps, sigma;       /* LJ parameters of Eq. (1) (1, 1) */
+    double eps, sigma;       /* LJ parameters of Eq. (1) (1, 1); Morse: eps, re */
+    int32_t potential;       /* lj_potential (LJ_POT_LJ = 0: Eq. (1)) */
+    double rho;              /* LJ_POT_MORSE: range parameter (> 0); unused for LJ */
 } lj_lbfgs_params;
 
 typedef struct {
@@ -240,6 +256,21 @@ const char* lj_ctx_last_error(const lj_ctx* ctx);
 lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
                                  lj_dtype xtype, const void* d_x, double* d_energy,
                                  void* d_grad, double eps, double sigma, void* stream);
+
+/*
+ * lj_energy_grad_batched for a chosen pair potential: potential LJ_POT_LJ
+ * gives exactly lj_energy_grad_batched (eps, sigma; rho unused);
+ * LJ_POT_MORSE evaluates E = eps sum_{i<j} e (e - 2), e = exp(rho (1 - r/re)),
+ * with re = sigma, and its gradient dE/dx_i = -(2 eps rho / re) sum_{j != i}
+ * e (e - 1) (x_i - x_j) / r_ij.  Morse clusters run one team per candidate
+ * in one-sided rows, FP32 (FP32 exp and reciprocal square root,
+ * compensated energy) or FP64.  Errors as lj_energy_grad_batched, plus
+ * INVALID_ARG for an unknown potential or rho <= 0 (Morse).
+ */
+lj_status lj_energy_grad_batched_pot(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
+                                     lj_dtype xtype, const void* d_x, double* d_energy,
+                                     void* d_grad, int32_t potential, double eps,
+                                     double sigma, double rho, void* stream);
 
 /*
  * Local minimisation of every candidate of `batch`, in place.

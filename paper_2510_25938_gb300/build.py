@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblj_bh.so")
 SOURCES = ["lj_api.cu", "lj_eval.cu", "lj_lbfgs_fp64.cu", "lj_lbfgs_mixed.cu", "lj_bh_fp64.cu",
-           "lj_bh_mixed.cu"]
+           "lj_bh_mixed.cu", "lj_morse_lbfgs_fp64.cu", "lj_morse_lbfgs_mixed.cu",
+           "lj_morse_bh_fp64.cu", "lj_morse_bh_mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-O2"]

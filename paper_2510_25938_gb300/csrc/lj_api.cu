@@ -143,6 +143,14 @@ lj_status check_batch(lj_ctx* ctx, const lj_batch* b, int* max_n) {
   return LJ_OK;
 }
 
+lj_status check_pot(lj_ctx* ctx, int32_t potential, double rho) {
+  if (potential != LJ_POT_LJ && potential != LJ_POT_MORSE)
+    return fail(ctx, LJ_ERR_INVALID_ARG, "unknown pair potential");
+  if (potential == LJ_POT_MORSE && !(rho > 0.0 && std::isfinite(rho)))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "Morse rho must be finite and > 0");
+  return LJ_OK;
+}
+
 lj_status check_min(lj_ctx* ctx, const lj_lbfgs_params* p) {
   if (!p) return fail(ctx, LJ_ERR_INVALID_ARG, "params is NULL");
   if (p->m < 1 || p->m > LJ_MAX_M) return fail(ctx, LJ_ERR_INVALID_ARG, "m outside 1..LJ_MAX_M");
@@ -158,7 +166,7 @@ lj_status check_min(lj_ctx* ctx, const lj_lbfgs_params* p) {
     return fail(ctx, LJ_ERR_INVALID_ARG, "switch_gtol must be >= 0 (0: automatic)");
   if (!(p->eps > 0.0 && std::isfinite(p->eps) && p->sigma > 0.0 && std::isfinite(p->sigma)))
     return fail(ctx, LJ_ERR_INVALID_ARG, "eps and sigma must be finite and > 0");
-  return LJ_OK;
+  return check_pot(ctx, p->potential, p->rho);
 }
 
 // size buckets of uneven batches (upper bounds, atoms); the autotuner keeps one
@@ -198,7 +206,7 @@ ljh::MinParamsH to_host(const lj_ctx* ctx, const lj_lbfgs_params* p, int bucket_
     const double t = bucket_n > 0 ? ctx->tune_sg[bucket_of(bucket_n)] : 0.0;
     h.switch_gtol = t > 0.0 ? t : kDefaultSwitchGtol;
   }
-  h.k = ljh::make_consts(p->eps, p->sigma);
+  h.k = ljh::make_consts(p->eps, p->sigma, p->potential, p->rho);
   h.df_one_sided = df_one_sided_for(ctx, bucket_n > 0 ? bucket_of(bucket_n) : -1);
   return h;
 }
@@ -330,6 +338,14 @@ const char* lj_ctx_last_error(const lj_ctx* ctx) {
 lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
                                  lj_dtype xtype, const void* d_x, double* d_energy, void* d_grad,
                                  double eps, double sigma, void* stream) {
+  return lj_energy_grad_batched_pot(ctx, batch, prec, xtype, d_x, d_energy, d_grad, LJ_POT_LJ,
+                                    eps, sigma, 0.0, stream);
+}
+
+lj_status lj_energy_grad_batched_pot(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
+                                     lj_dtype xtype, const void* d_x, double* d_energy,
+                                     void* d_grad, int32_t potential, double eps, double sigma,
+                                     double rho, void* stream) {
   if (!ctx) return LJ_ERR_INVALID_ARG;
   int max_n = 0;
   lj_status st = check_batch(ctx, batch, &max_n);
@@ -339,6 +355,8 @@ lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precisio
   if (xtype != LJ_F32 && xtype != LJ_F64) return fail(ctx, LJ_ERR_INVALID_ARG, "bad dtype");
   if (!(eps > 0.0 && std::isfinite(eps) && sigma > 0.0 && std::isfinite(sigma)))
     return fail(ctx, LJ_ERR_INVALID_ARG, "eps and sigma must be finite and > 0");
+  st = check_pot(ctx, potential, rho);
+  if (st != LJ_OK) return st;
   if (batch->n_cand == 0) return LJ_OK;
   if (!d_x || !d_energy) return fail(ctx, LJ_ERR_INVALID_ARG, "d_x and d_energy are required");
   const size_t el = xtype == LJ_F32 ? 4 : 8;
@@ -356,7 +374,7 @@ lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precisio
   a.x = d_x;
   a.energy = d_energy;
   a.grad = d_grad;
-  a.k = ljh::make_consts(eps, sigma);
+  a.k = ljh::make_consts(eps, sigma, potential, rho);
   cudaError_t e = ljh::eval_launch(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lj_energy_grad_batched launch");
   return LJ_OK;
@@ -384,8 +402,8 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   auto plan_for = [&](int bound, ljh::Plan* pl) {
     const int team = ctx->lbfgs_team ? ctx->lbfgs_team : ctx->tune_team[bucket_of(bound)];
     const bool hg = hist_global_for(ctx, bucket_of(bound));
-    return mixed ? ljh::lbfgs_plan_mixed(bound, p->m, batch->n_cand, ctx->device, team, pl, hg)
-                 : ljh::lbfgs_plan_fp64(bound, p->m, batch->n_cand, ctx->device, team, pl, hg);
+    return ljh::lbfgs_plan(mixed, p->potential, bound, p->m, batch->n_cand, ctx->device, team,
+                           pl, hg);
   };
   if (batch->uniform_n == 0 && max_n > 32 && batch->n_cand > 1) {
     // Uneven batch spanning several size classes: sort candidates into size
@@ -433,8 +451,7 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
       a.hist_on_chip = plans[b].hist_on_chip;
       a.list = lists + (size_t)b * batch->n_cand;
       a.list_count = counts + b;
-      e = mixed ? ljh::lbfgs_launch_mixed(a, plans[b], (cudaStream_t)stream)
-                : ljh::lbfgs_launch_fp64(a, plans[b], (cudaStream_t)stream);
+      e = ljh::lbfgs_launch(a, plans[b], (cudaStream_t)stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
     }
     return LJ_OK;
@@ -461,8 +478,7 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
   a.hist = ctx->ws;
   a.hist_slot_bytes = plan.slot_bytes;
   a.hist_on_chip = plan.hist_on_chip;
-  e = mixed ? ljh::lbfgs_launch_mixed(a, plan, (cudaStream_t)stream)
-            : ljh::lbfgs_launch_fp64(a, plan, (cudaStream_t)stream);
+  e = ljh::lbfgs_launch(a, plan, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
   return LJ_OK;
 }
@@ -499,10 +515,8 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   if (!(minp.switch_gtol > 0.0) && ctx->bh_tuned && ctx->bh_tune_sg > 0.0)
     minp.switch_gtol = ctx->bh_tune_sg;
   ljh::Plan plan;
-  cudaError_t e = mixed ? ljh::bh_plan_mixed(s->n_atoms, p->min.m, s->n_walkers, p->K, team,
-                                             &plan, hg)
-                        : ljh::bh_plan_fp64(s->n_atoms, p->min.m, s->n_walkers, p->K, team,
-                                            &plan, hg);
+  cudaError_t e = ljh::bh_plan(mixed, p->min.potential, s->n_atoms, p->min.m, s->n_walkers, p->K,
+                                team, &plan, hg);
   if (e == cudaErrorNotSupported)
     return fail(ctx, LJ_ERR_UNSUPPORTED,
                 "bh_step_batched supports clusters of up to 256 atoms in this build");
@@ -528,8 +542,7 @@ lj_status bh_step_batched(lj_ctx* ctx, const lj_bh_state* s, const lj_bh_params*
   a.hist = ctx->ws;
   a.hist_slot_bytes = plan.slot_bytes;
   a.hist_on_chip = plan.hist_on_chip;
-  e = mixed ? ljh::bh_launch_mixed(a, plan, (cudaStream_t)stream)
-            : ljh::bh_launch_fp64(a, plan, (cudaStream_t)stream);
+  e = ljh::bh_launch(a, plan, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "bh_step_batched launch");
   return LJ_OK;
 }
@@ -621,7 +634,7 @@ struct Tuner {
     lj_lbfgs_params p;
     p.m = m; p.gtol = 1e-6; p.max_iter = 15000; p.max_ls = 20; p.c1 = 1e-3; p.c2 = 0.9;
     p.alpha_max = 1e10; p.prec = prec; p.switch_gtol = kDefaultSwitchGtol;
-    p.deadline_cycles = 0; p.eps = 1.0; p.sigma = 1.0;
+    p.deadline_cycles = 0; p.eps = 1.0; p.sigma = 1.0; p.potential = LJ_POT_LJ; p.rho = 0.0;
     *team = kTuneChoices[b][0];
     if (kTuneChoices[b][1] != 0) {
       double best = -1.0;
@@ -650,9 +663,8 @@ struct Tuner {
     *hist = 0;
     *df = 0;
     ljh::Plan pl;
-    cudaError_t e = prec == LJ_PREC_MIXED
-                        ? ljh::lbfgs_plan_mixed(nt, m, nc, ctx->device, *team, &pl, false)
-                        : ljh::lbfgs_plan_fp64(nt, m, nc, ctx->device, *team, &pl, false);
+    cudaError_t e = ljh::lbfgs_plan(prec == LJ_PREC_MIXED, LJ_POT_LJ, nt, m, nc, ctx->device,
+                                    *team, &pl, false);
     if (e != cudaSuccess) return fail(ctx, LJ_ERR_CUDA, "autotune: plan failed");
     if (pl.hist_on_chip) {                 // the alternative: history in global memory
       ctx->hist_opt = 1;
@@ -879,8 +891,8 @@ lj_status lj_ctx_autotune_bh(lj_ctx* ctx, const lj_bh_state* state, const lj_bh_
     }
     if (rc == LJ_OK) {                            // history in global memory
       ljh::Plan pl;
-      cudaError_t e = mixed ? ljh::bh_plan_mixed(n, p->min.m, W, p->K, best_team, &pl, false)
-                            : ljh::bh_plan_fp64(n, p->min.m, W, p->K, best_team, &pl, false);
+      cudaError_t e = ljh::bh_plan(mixed, p->min.potential, n, p->min.m, W, p->K, best_team, &pl,
+                                   false);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "autotune_bh plan");
       if (rc == LJ_OK && pl.hist_on_chip) {
         double r = 0.0;
@@ -944,8 +956,8 @@ lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_p
   }
   ljh::Plan plans[ljh::kMaxBuckets];
   for (int b = 0; b < nb; ++b) {
-    cudaError_t e = mixed ? ljh::lbfgs_plan_mixed(bk.bound[b], p->m, batch->n_cand, dev, 0, &plans[b])
-                          : ljh::lbfgs_plan_fp64(bk.bound[b], p->m, batch->n_cand, dev, 0, &plans[b]);
+    cudaError_t e = ljh::lbfgs_plan(mixed, p->potential, bk.bound[b], p->m, batch->n_cand, dev, 0,
+                                    &plans[b]);
     if (e != cudaSuccess) return LJ_ERR_CUDA;
     if (!plans[b].hist_on_chip) {
       // launch only as many teams as the scratch holds history slots for
@@ -982,8 +994,7 @@ lj_status lbfgs_minimize_batched_noalloc(const lj_batch* batch, const lj_lbfgs_p
       a.list = lists + (size_t)b * batch->n_cand;
       a.list_count = counts + b;
     }
-    cudaError_t e = mixed ? ljh::lbfgs_launch_mixed(a, plans[b], (cudaStream_t)stream)
-                          : ljh::lbfgs_launch_fp64(a, plans[b], (cudaStream_t)stream);
+    cudaError_t e = ljh::lbfgs_launch(a, plans[b], (cudaStream_t)stream);
     if (e != cudaSuccess) return LJ_ERR_CUDA;
   }
   return LJ_OK;

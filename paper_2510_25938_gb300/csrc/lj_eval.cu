@@ -1,4 +1,5 @@
-// lj_eval.cu -- lj_energy_grad_batched: batched Eq. (1) energy + gradient.
+// lj_eval.cu -- lj_energy_grad_batched: batched Eq. (1) energy + gradient
+// (and the Morse pair potential through the team kernel).
 //
 // Uniform batches (2..512 atoms): flat layout, one thread per atom, several
 // whole candidates per 512-thread CTA.  Uneven batches: one team per
@@ -14,7 +15,7 @@ namespace {
 
 using namespace ljd;
 
-template <int T, int A, typename X, typename IO>
+template <int T, int A, typename X, typename IO, int POT = LJ_POT_LJ>
 __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int TPC = cta_threads_for(T) / T;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(cta_threads_for(T)) eval_kernel(ljh::EvalArgs 
     }
     typename Tr<X>::F E;
     typename Tr<X>::S dummy;
-    evaluate<T, A, Prec<X, X, X, 0>>(tm, n, x, g, pos, nullptr, p, nullptr, E, dummy);
+    evaluate<T, A, Prec<X, X, X, 0, POT>>(tm, n, x, g, pos, nullptr, p, nullptr, E, dummy);
     if (gout) {
 #pragma unroll
       for (int s = 0; s < A; ++s) {
@@ -769,12 +770,12 @@ cudaError_t launch_flat_f64(const ljh::EvalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int T, int A, typename X, typename IO>
+template <int T, int A, typename X, typename IO, int POT = LJ_POT_LJ>
 cudaError_t launch_one(const ljh::EvalArgs& a, cudaStream_t s) {
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
   const size_t smem = TPC * team_smem_bytes<T>(a.max_n, false);
-  auto k = eval_kernel<T, A, X, IO>;
+  auto k = eval_kernel<T, A, X, IO, POT>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -797,6 +798,18 @@ cudaError_t launch_one(const ljh::EvalArgs& a, cudaStream_t s) {
 namespace ljh {
 
 cudaError_t eval_launch(const EvalArgs& a, cudaStream_t s) {
+  if (a.k.pot == LJ_POT_MORSE) {
+    // Morse: one team per candidate, one-sided rows, any batch layout
+    return dispatch_team(a.max_n, [&](auto TT, auto AA) -> cudaError_t {
+      constexpr int T = decltype(TT)::value;
+      constexpr int A = decltype(AA)::value;
+      constexpr int M = LJ_POT_MORSE;
+      const bool fp64 = a.prec == LJ_PREC_FP64;
+      if (a.xtype == LJ_F32)
+        return fp64 ? launch_one<T, A, double, float, M>(a, s) : launch_one<T, A, float, float, M>(a, s);
+      return fp64 ? launch_one<T, A, double, double, M>(a, s) : launch_one<T, A, float, double, M>(a, s);
+    });
+  }
   // uniform batches of 2..512 atoms: flat thread-per-atom layout
   if (a.uniform_n >= 2 && a.uniform_n <= kFlatThreads) {
     const bool fp64 = a.prec == LJ_PREC_FP64;

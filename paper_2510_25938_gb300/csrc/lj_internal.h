@@ -15,7 +15,7 @@ struct MinParamsH {     // mirror of ljd::MinParams (plain data)
   int m, max_iter, max_ls;
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
-  LjConsts k;             // Eq. (1) constants from eps and sigma
+  LjConsts k;             // pair-potential constants (Eq. (1) or Morse)
   double f32_resolution, df_resolution;   // handover thresholds, relative to |E|
   int df_one_sided = 0;   // double-float evaluations in one-sided rows even where
                           // the team could use tiles (clusters above 256 atoms)
@@ -31,7 +31,7 @@ struct EvalArgs {
   const void* x;
   double* energy;
   void* grad;
-  LjConsts k;           // Eq. (1) constants from eps and sigma
+  LjConsts k;           // pair-potential constants (Eq. (1) or Morse)
 };
 
 struct LbfgsArgs {
@@ -118,5 +118,47 @@ cudaError_t bh_plan_mixed(int n_atoms, int m, int n_walkers, int K, int team, Pl
                           bool hist_global = false);
 cudaError_t bh_launch_fp64(const BhArgs& a, const Plan& plan, cudaStream_t s);
 cudaError_t bh_launch_mixed(const BhArgs& a, const Plan& plan, cudaStream_t s);
+
+// the same kernels on the Morse pair potential (lj_morse_*.cu)
+cudaError_t lbfgs_plan_morse_fp64(int max_n, int m, int64_t n_cand, int device, int team,
+                                  Plan* out, bool hist_global);
+cudaError_t lbfgs_plan_morse_mixed(int max_n, int m, int64_t n_cand, int device, int team,
+                                   Plan* out, bool hist_global);
+cudaError_t lbfgs_launch_morse_fp64(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t lbfgs_launch_morse_mixed(const LbfgsArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t bh_plan_morse_fp64(int n_atoms, int m, int n_walkers, int K, int team, Plan* out,
+                               bool hist_global);
+cudaError_t bh_plan_morse_mixed(int n_atoms, int m, int n_walkers, int K, int team, Plan* out,
+                                bool hist_global);
+cudaError_t bh_launch_morse_fp64(const BhArgs& a, const Plan& plan, cudaStream_t s);
+cudaError_t bh_launch_morse_mixed(const BhArgs& a, const Plan& plan, cudaStream_t s);
+
+// plan / launch by precision and pair potential
+inline cudaError_t lbfgs_plan(bool mixed, int pot, int max_n, int m, int64_t n_cand, int device,
+                              int team, Plan* out, bool hist_global = false) {
+  if (pot == LJ_POT_MORSE)
+    return mixed ? lbfgs_plan_morse_mixed(max_n, m, n_cand, device, team, out, hist_global)
+                 : lbfgs_plan_morse_fp64(max_n, m, n_cand, device, team, out, hist_global);
+  return mixed ? lbfgs_plan_mixed(max_n, m, n_cand, device, team, out, hist_global)
+               : lbfgs_plan_fp64(max_n, m, n_cand, device, team, out, hist_global);
+}
+inline cudaError_t lbfgs_launch(const LbfgsArgs& a, const Plan& plan, cudaStream_t s) {
+  if (a.p.k.pot == LJ_POT_MORSE)
+    return a.mixed ? lbfgs_launch_morse_mixed(a, plan, s) : lbfgs_launch_morse_fp64(a, plan, s);
+  return a.mixed ? lbfgs_launch_mixed(a, plan, s) : lbfgs_launch_fp64(a, plan, s);
+}
+inline cudaError_t bh_plan(bool mixed, int pot, int n_atoms, int m, int n_walkers, int K,
+                           int team, Plan* out, bool hist_global = false) {
+  if (pot == LJ_POT_MORSE)
+    return mixed ? bh_plan_morse_mixed(n_atoms, m, n_walkers, K, team, out, hist_global)
+                 : bh_plan_morse_fp64(n_atoms, m, n_walkers, K, team, out, hist_global);
+  return mixed ? bh_plan_mixed(n_atoms, m, n_walkers, K, team, out, hist_global)
+               : bh_plan_fp64(n_atoms, m, n_walkers, K, team, out, hist_global);
+}
+inline cudaError_t bh_launch(const BhArgs& a, const Plan& plan, cudaStream_t s) {
+  if (a.p.k.pot == LJ_POT_MORSE)
+    return a.mixed ? bh_launch_morse_mixed(a, plan, s) : bh_launch_morse_fp64(a, plan, s);
+  return a.mixed ? bh_launch_mixed(a, plan, s) : bh_launch_fp64(a, plan, s);
+}
 
 }  // namespace ljh

@@ -26,9 +26,12 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
 // Register budget: teams for more than 256 atoms (which carry the tiled
 // double-float evaluation) are allowed all registers of one CTA per SM; the
 // others are left to the compiler's own occupancy choice.
-template <int T, int A, bool MIXED>
+// POT: pair potential (LJ_POT_LJ, Eq. (1); LJ_POT_MORSE).  Morse teams keep
+// no half-pair buffer (their evaluations are one-sided rows).
+template <int T, int A, bool MIXED, int POT = LJ_POT_LJ>
 __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
     lbfgs_kernel(ljh::LbfgsArgs a) {
+  constexpr bool kHalf = POT == LJ_POT_LJ;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int TPC = cta_threads_for(T) / T;
   const int team = threadIdx.x / T;
@@ -40,7 +43,7 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
   void* hbuf;
   void* hist;
   const size_t hb = a.hist_on_chip ? a.hist_slot_bytes : 0;
-  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true, hb), a.max_n, true, hb, pos,
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, kHalf, hb), a.max_n, kHalf, hb, pos,
                 hbuf, hist, tm.red, word);
   MinParams p = to_dev(a.p);
   // hbuf: pair buffer up to 64 atoms, tile accumulators above 256.  With
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
       for (int k = 0; k < 3; ++k) x64[s][k] = i < n ? a.x[3 * (a0 + i) + k] : 0.0;
     }
     MinResult r;
-    minimise<T, A, MIXED>(tm, n, x64, p, hist, pos, hbuf, r);
+    minimise<T, A, MIXED, POT>(tm, n, x64, p, hist, pos, hbuf, r);
 #pragma unroll
     for (int s = 0; s < A; ++s) {
       const int i = tm.rank + s * T;
@@ -134,16 +137,17 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
   }
 }
 
-template <int T, int A, bool MIXED>
+template <int T, int A, bool MIXED, int POT>
 cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out,
                      bool hist_global) {
+  constexpr bool kHalf = POT == LJ_POT_LJ;
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
   const size_t hist_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
   const bool on_chip =
-      !hist_global && TPC * team_smem_bytes<T>(max_n, true, hist_bytes) <= kSmemBudget;
-  const size_t smem = TPC * team_smem_bytes<T>(max_n, true, on_chip ? hist_bytes : 0);
-  auto k = lbfgs_kernel<T, A, MIXED>;
+      !hist_global && TPC * team_smem_bytes<T>(max_n, kHalf, hist_bytes) <= kSmemBudget;
+  const size_t smem = TPC * team_smem_bytes<T>(max_n, kHalf, on_chip ? hist_bytes : 0);
+  auto k = lbfgs_kernel<T, A, MIXED, POT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int sms = 0, per_sm = 0;
@@ -210,23 +214,23 @@ cudaError_t dispatch_lb(int max_n, int team, F&& f) {
   return dispatch_team(max_n, f);
 }
 
-template <bool MIXED>
+template <bool MIXED, int POT = LJ_POT_LJ>
 cudaError_t plan_impl(int max_n, int m, int64_t n_cand, int device, int team, ljh::Plan* out,
                       bool hist_global) {
   return dispatch_lb(max_n, team, [&](auto TT, auto AA) -> cudaError_t {
-    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED>(max_n, m, n_cand, device, out,
-                                                                     hist_global);
+    return plan_one<decltype(TT)::value, decltype(AA)::value, MIXED, POT>(max_n, m, n_cand, device,
+                                                                          out, hist_global);
   });
 }
 
-template <bool MIXED>
+template <bool MIXED, int POT = LJ_POT_LJ>
 cudaError_t launch_impl(const ljh::LbfgsArgs& a, const ljh::Plan& plan, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   return dispatch_lb(a.max_n, plan.team, [&](auto TT, auto AA) -> cudaError_t {
     constexpr int T = decltype(TT)::value;
     constexpr int A = decltype(AA)::value;
-    lbfgs_kernel<T, A, MIXED><<<plan.grid, cta_threads_for(T), plan.smem, s>>>(a);
+    lbfgs_kernel<T, A, MIXED, POT><<<plan.grid, cta_threads_for(T), plan.smem, s>>>(a);
     return cudaGetLastError();
   });
 }

@@ -44,7 +44,7 @@ struct MinParams {
   int m, max_iter, max_ls;
   double gtol, c1, c2, alpha_max, switch_gtol;
   long long deadline;
-  ljh::LjConsts k;         // Eq. (1) constants from eps and sigma (host-derived)
+  ljh::LjConsts k;         // pair-potential constants (host-derived)
   int tiled;               // hbuf holds tile accumulators (teams for > 64 atoms), not pairs
   double f32_resolution;   // FP32 phase hands over below this predicted decrease / |E|
   double df_resolution;    // double-float polish hands over below this / |E|
@@ -72,12 +72,13 @@ constexpr int kFP32GradIters = 2000;
 //   directions and history, PM pair arithmetic (0: XP's own, 1: double-float).
 //   S line-search scalars: FP64 only on the all-FP64 path.  F energies: FP64
 //   when positions are FP64, float-float otherwise (FP32 pipes only).
-template <typename XP_, typename XG_, typename V_, int PM_>
+template <typename XP_, typename XG_, typename V_, int PM_, int POT_ = LJ_POT_LJ>
 struct Prec {
   using XP = XP_;
   using XG = XG_;
   using V = V_;
   static constexpr int PM = PM_;
+  static constexpr int POT = POT_;   // pair potential: LJ_POT_LJ or LJ_POT_MORSE
   using S = std::conditional_t<sizeof(V_) == 8, double, float>;
   using F = std::conditional_t<std::is_same<XP_, double>::value, double, ff>;
 };
@@ -127,6 +128,135 @@ __device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
 // double-float arithmetic on coordinates scaled by 1/sigma.
 // hbuf: the team's half-pair buffer (24 bytes per pair) or nullptr; used for
 // FP64 / double-float evaluations, which then compute each pair once.
+// ---------------------------------------------------------------------------
+// Morse pair potential (Morse 1929, cluster form), the pair-potential
+// extension of the method: V(r) = eps e (e - 2), e = exp(rho (1 - r / re)),
+// re in the sigma slot.  One-sided rows: every thread sums, for each atom it
+// owns, the terms of all other atoms (deterministic, no shared pair buffer);
+// E = (eps / 2) sum_i sum_{j != i} e (e - 2), and
+// g_i = -(2 eps rho / re) sum_{j != i} e (e - 1) (x_i - x_j) / r.
+// FP32 (first tier of the mixed path; compensated energy) and FP64; the
+// mixed path has no double-float tier for this potential.  Coincident atoms
+// give E = +inf (and a non-finite gradient), as for Eq. (1).
+// ---------------------------------------------------------------------------
+template <int T, int A, typename P>
+__device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
+                                               const typename P::XP (&x)[A][3],
+                                               typename P::XG (&g)[A][3], void* posv,
+                                               const MinParams& p,
+                                               const typename P::V (*d)[3],
+                                               typename P::F& E, typename P::S& dphi) {
+  using X = typename P::XP;
+  using V = typename P::V;
+  using S = typename P::S;
+  static_assert(P::PM == 0, "Morse pair terms are evaluated in FP32 or FP64 only");
+  using Q = typename PosOf<X>::type;
+  Q* pos = static_cast<Q*>(posv);
+  tm.sync();  // previous readers of pos are done
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int i = tm.rank + a * T;
+    if (i < n) {
+      Q q;
+      q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
+      pos[i] = q;
+    }
+  }
+  tm.sync();
+  V dp = (V)0;
+  if constexpr (sizeof(X) == 4) {
+    const float rho = p.k.rho_f, rr = p.k.rho_re_f, gsc = p.k.m_g_f;
+    const float kInfF = __int_as_float(0x7f800000);
+    ff e{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int i = tm.rank + a * T;
+      if (i < n) {
+        const float xi = x[a][0], yi = x[a][1], zi = x[a][2];
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        ff ea{0.f, 0.f};
+#pragma unroll 2
+        for (int j = 0; j < n; ++j) {
+          const Q q = pos[j];
+          const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float ir = rsqrtf(r2);
+          const float ex = __expf(fmaf(-rr, r2 * ir, rho));   // e^{rho (1 - r/re)}
+          float term = ex * (ex - 2.f);
+          float c = ex * (ex - 1.f) * ir;
+          if (j == i) {
+            term = 0.f;
+            c = 0.f;
+          } else if (!(r2 > 0.f)) {
+            term = kInfF;
+          }
+          ea = ff_add_f(ea, term);
+          ax = fmaf(c, dx, ax);
+          ay = fmaf(c, dy, ay);
+          az = fmaf(c, dz, az);
+        }
+        g[a][0] = -gsc * ax; g[a][1] = -gsc * ay; g[a][2] = -gsc * az;
+        e = ff_add(e, ea);
+      } else {
+        g[a][0] = 0.f; g[a][1] = 0.f; g[a][2] = 0.f;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    if constexpr (std::is_same<V, float>::value) {
+      if (d) {                  // energy and g.d in one team reduction
+        team_sum_ff_f<T>(tm, e, dp);
+        E = ff_scale(e, p.k.m_half_f);
+        dphi = (S)dp;
+        return;
+      }
+    }
+    E = ff_scale(team_sum_ff<T>(tm, e), p.k.m_half_f);
+  } else {
+    const double rho = p.k.rho, rr = p.k.rho_re, gsc = p.k.m_g;
+    const double kInf = __longlong_as_double(0x7ff0000000000000LL);
+    dd e{0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int i = tm.rank + a * T;
+      if (i < n) {
+        const double xi = x[a][0], yi = x[a][1], zi = x[a][2];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        double eb = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const Q q = pos[j];
+          const double dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+          const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+          const double r = sqrt(r2);
+          const double ex = exp(fma(-rr, r, rho));
+          double term = ex * (ex - 2.0);
+          double c = ex * (ex - 1.0) / r;
+          if (j == i) {
+            term = 0.0;
+            c = 0.0;
+          } else if (!(r2 > 0.0)) {
+            term = kInf;
+          }
+          const dd t = dd_two_sum(eb, term);      // compensated row energy
+          eb = t.hi;
+          e.lo = __dadd_rn(e.lo, t.lo);
+          ax = fma(c, dx, ax);
+          ay = fma(c, dy, ay);
+          az = fma(c, dz, az);
+        }
+        const dd t = dd_two_sum(e.hi, eb);
+        e.hi = t.hi;
+        e.lo = __dadd_rn(e.lo, t.lo);
+        g[a][0] = -gsc * ax; g[a][1] = -gsc * ay; g[a][2] = -gsc * az;
+      } else {
+        g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    E = team_sum_dd<T>(tm, e) * p.k.m_half;
+  }
+  if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+}
+
 template <int T, int A, typename P>
 __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
                                          const typename P::XP (&x)[A][3],
@@ -138,6 +268,10 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   using V = typename P::V;
   using S = typename P::S;
   constexpr int PM = P::PM;
+  if constexpr (P::POT != LJ_POT_LJ) {
+    evaluate_morse<T, A, P>(tm, n, x, g, posv, p, d, E, dphi);
+    return;
+  }
   tm.sync();  // previous readers of pos are done
 #pragma unroll
   for (int a = 0; a < A; ++a) {
@@ -1085,9 +1219,13 @@ __device__ __forceinline__ int status_of(int code) {
        : code == PH_TIMEOUT  ? ST_TIMEOUT : ST_MAXITER;
 }
 
-template <int T, int A, bool MIXED>
+template <int T, int A, bool MIXED, int POT = LJ_POT_LJ>
 __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)[A][3], const MinParams& p,
                          void* hist, void* pos, void* hbuf, MinResult& r) {
+  using P32 = Prec<float, float, float, 0, POT>;       // mixed: FP32 tier
+  using PDF = Prec<ff, float, float, 1, POT>;          // mixed: double-float tier
+  using P64m = Prec<double, double, float, 0, POT>;    // mixed: FP64 tier
+  using P64 = Prec<double, double, double, 0, POT>;    // FP64 path
   r.E = 0.0; r.status = ST_CONVERGED; r.iters = 0;
   r.evals32 = 0; r.evals64 = 0; r.evals_df = 0; r.iters32 = 0; r.iters64 = 0;
   r.vec32 = 0; r.vec64 = 0;
@@ -1109,7 +1247,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
   if constexpr (!MIXED) {
     double g[A][3];
     double f, dummy;
-    evaluate<T, A, PrecF64>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
+    evaluate<T, A, P64>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
     r.evals64 = 1;
     const double gm = grad_max<T, A, double>(tm, g);
     if (!isfinite(f) || !(gm < kInf)) {
@@ -1118,7 +1256,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
     if (gm < p.gtol) { r.E = f; lap(r.cyc64); return; }
     double rho[LJ_MAX_M], gmv[LJ_MAX_M], sup[LJ_MAX_M];
     double* Sh = (double*)hist;
-    const int code = run_phase<T, A, PrecF64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, rho, gmv, sup, cnt,
+    const int code = run_phase<T, A, P64, 0>(tm, n, x64, g, f, Sh, Sh + hstride, rho, gmv, sup, cnt,
                                                  head, iters, r.evals64, r.iters64, r.vec64, pos,
                                                  hbuf, p, t0, cyc);
     r.E = f;
@@ -1141,11 +1279,11 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
 #pragma unroll
         for (int c = 0; c < 3; ++c) x32[a][c] = (float)x64[a][c];
       ff f32;
-      evaluate<T, A, PrecF32>(tm, n, x32, g32, pos, nullptr, p, nullptr, f32, dummy32);
+      evaluate<T, A, P32>(tm, n, x32, g32, pos, nullptr, p, nullptr, f32, dummy32);
       r.evals32 = 1;
       const float gm = grad_max<T, A, float>(tm, g32);
       if (fisfinite(f32) && gm < __int_as_float(0x7f800000) && !(gm < (float)p.switch_gtol)) {
-        code = run_phase<T, A, PrecF32, 1>(tm, n, x32, g32, f32, Sh, Yh, rho, gmv, sup, cnt, head,
+        code = run_phase<T, A, P32, 1>(tm, n, x32, g32, f32, Sh, Yh, rho, gmv, sup, cnt, head,
                                            iters, r.evals32, r.iters32, r.vec32, pos, nullptr, p,
                                            t0, cyc);
         moved32 = r.iters32 > 0;
@@ -1162,6 +1300,15 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
 #pragma unroll
           for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
       }
+    } else if constexpr (POT != LJ_POT_LJ) {
+      // no double-float tier for this potential: FP32 hands over to FP64
+      if (moved32) {
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
+      }
+      need_fp64 = true;
     } else {
       // ---- tier 2: double-float positions and pair terms, FP32 elsewhere -----
       ff xdf[A][3];
@@ -1172,7 +1319,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
         for (int c = 0; c < 3; ++c)
           xdf[a][c] = moved32 ? ff{x32[a][c], 0.f} : df_from_double(x64[a][c]);
       ff fdf;
-      evaluate<T, A, PrecDF>(tm, n, xdf, gdf, pos, hbuf, p, nullptr, fdf, dummy32);
+      evaluate<T, A, PDF>(tm, n, xdf, gdf, pos, hbuf, p, nullptr, fdf, dummy32);
       r.evals_df += 1;
       float gm = grad_max<T, A, float>(tm, gdf);
       if (!fisfinite(fdf) || !(gm < __int_as_float(0x7f800000))) need_fp64 = true;
@@ -1181,7 +1328,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
           need_fp64 = true;               // confirm (and finish) in FP64
           break;
         }
-        code = run_phase<T, A, PrecDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, rho, gmv, sup, cnt, head, iters,
+        code = run_phase<T, A, PDF, 2>(tm, n, xdf, gdf, fdf, Sh, Yh, rho, gmv, sup, cnt, head, iters,
                                           r.evals_df, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
         if (code == PH_CONVERGED) {
           gm = 0.f;
@@ -1201,7 +1348,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
     double f, dummy;
     if (need_fp64) {
       // ---- tier 3: FP64 -------------------------------------------------------
-      evaluate<T, A, PrecF64m>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy32);
+      evaluate<T, A, P64m>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy32);
       r.evals64 += 1;
       const double gm = grad_max<T, A, double>(tm, g);
       if (!isfinite(f) || !(gm < kInf)) {
@@ -1210,7 +1357,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
       if (gm < p.gtol) {
         r.E = f; r.iters = iters; r.status = ST_CONVERGED; lap(r.cyc64); return;
       }
-      code = run_phase<T, A, PrecF64m, 0>(tm, n, x64, g, f, Sh, Yh, rho, gmv, sup, cnt, head, iters,
+      code = run_phase<T, A, P64m, 0>(tm, n, x64, g, f, Sh, Yh, rho, gmv, sup, cnt, head, iters,
                                           r.evals64, r.iters64, r.vec64, pos, hbuf, p, t0, cyc);
       r.E = f;
       r.iters = iters;
@@ -1219,7 +1366,7 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
       return;
     }
     // final energy (and the non-finite test) in FP64
-    evaluate<T, A, PrecF64>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
+    evaluate<T, A, P64>(tm, n, x64, g, pos, hbuf, p, nullptr, f, dummy);
     r.evals64 += 1;
     const double gm = grad_max<T, A, double>(tm, g);
     r.E = f;

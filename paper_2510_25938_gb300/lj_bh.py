@@ -21,6 +21,7 @@ from . import build as _build
 LJ_OK, LJ_ERR_INVALID_ARG, LJ_ERR_CUDA, LJ_ERR_NO_WORKSPACE, LJ_ERR_UNSUPPORTED = 0, -1, -2, -3, -4
 LJ_F32, LJ_F64 = 0, 1
 LJ_PREC_FP64, LJ_PREC_FP32, LJ_PREC_MIXED = 0, 1, 2
+LJ_POT_LJ, LJ_POT_MORSE = 0, 1
 (LJ_CAND_CONVERGED, LJ_CAND_MAXITER, LJ_CAND_LINESEARCH_FAIL, LJ_CAND_NONFINITE,
  LJ_CAND_TIMEOUT, LJ_CAND_BAD_INPUT) = range(6)
 LJ_MAX_ATOMS, LJ_MAX_M, LJ_MAX_K = 1024, 32, 16
@@ -48,7 +49,8 @@ class _Lbfgs(C.Structure):
     _fields_ = [("m", C.c_int32), ("gtol", C.c_double), ("max_iter", C.c_int32),
                 ("max_ls", C.c_int32), ("c1", C.c_double), ("c2", C.c_double),
                 ("alpha_max", C.c_double), ("prec", C.c_int), ("switch_gtol", C.c_double),
-                ("deadline_cycles", C.c_int64), ("eps", C.c_double), ("sigma", C.c_double)]
+                ("deadline_cycles", C.c_int64), ("eps", C.c_double), ("sigma", C.c_double),
+                ("potential", C.c_int32), ("rho", C.c_double)]
 
 
 class _Bh(C.Structure):
@@ -111,6 +113,10 @@ def load():
             lib.lj_energy_grad_batched.argtypes = [P, C.POINTER(_Batch), C.c_int, C.c_int, P, P,
                                                    P, C.c_double, C.c_double, P]
             lib.lj_energy_grad_batched.restype = C.c_int
+            lib.lj_energy_grad_batched_pot.argtypes = [P, C.POINTER(_Batch), C.c_int, C.c_int,
+                                                       P, P, P, C.c_int32, C.c_double,
+                                                       C.c_double, C.c_double, P]
+            lib.lj_energy_grad_batched_pot.restype = C.c_int
             lib.lbfgs_minimize_batched.argtypes = [P, C.POINTER(_Batch), C.POINTER(_Lbfgs), P, P,
                                                    P, P, P, P, P]
             lib.lbfgs_minimize_batched.restype = C.c_int
@@ -251,12 +257,14 @@ class LbfgsParams:
     switch_gtol: float = 0.0       # 0: automatic (autotuned per bucket, else 1e-3)
     deadline_cycles: int = 0
     eps: float = 1.0
-    sigma: float = 1.0
+    sigma: float = 1.0             # Morse: re
+    potential: int = LJ_POT_LJ     # or LJ_POT_MORSE
+    rho: float = 6.0               # Morse range (unused for LJ)
 
     def c(self) -> _Lbfgs:
         return _Lbfgs(self.m, self.gtol, self.max_iter, self.max_ls, self.c1, self.c2,
                       self.alpha_max, self.prec, self.switch_gtol, self.deadline_cycles,
-                      self.eps, self.sigma)
+                      self.eps, self.sigma, self.potential, self.rho)
 
 
 @dataclass
@@ -301,8 +309,9 @@ def lj_energy_grad_batched(ctx: Ctx, x: torch.Tensor, energy: torch.Tensor,
                            grad: torch.Tensor | None = None, *, n_cand: int, uniform_n: int = 0,
                            atom_offset: torch.Tensor | None = None, max_n: int = 0,
                            prec: int = LJ_PREC_FP64, eps: float = 1.0, sigma: float = 1.0,
-                           stream=None):
-    """Eq. (1) energies (float64 [n_cand]) and gradients (x's dtype) of a batch."""
+                           potential: int = LJ_POT_LJ, rho: float = 6.0, stream=None):
+    """Energies (float64 [n_cand]) and gradients (x's dtype) of a batch: Eq. (1),
+    or the Morse potential with potential=LJ_POT_MORSE (sigma = re, range rho)."""
     if x.dtype not in (torch.float32, torch.float64):
         raise ValueError("x must be float32 or float64")
     if energy.dtype != torch.float64:
@@ -311,8 +320,13 @@ def lj_energy_grad_batched(ctx: Ctx, x: torch.Tensor, energy: torch.Tensor,
         raise ValueError("grad must have x's dtype")
     xt = LJ_F32 if x.dtype == torch.float32 else LJ_F64
     b = _batch(n_cand, uniform_n, atom_offset, max_n)
-    st = load().lj_energy_grad_batched(ctx.handle, C.byref(b), prec, xt, _ptr(x), _ptr(energy),
-                                       _ptr(grad), eps, sigma, _stream(stream))
+    if potential == LJ_POT_LJ:
+        st = load().lj_energy_grad_batched(ctx.handle, C.byref(b), prec, xt, _ptr(x),
+                                           _ptr(energy), _ptr(grad), eps, sigma, _stream(stream))
+    else:
+        st = load().lj_energy_grad_batched_pot(ctx.handle, C.byref(b), prec, xt, _ptr(x),
+                                               _ptr(energy), _ptr(grad), potential, eps, sigma,
+                                               rho, _stream(stream))
     _check(ctx, st, "lj_energy_grad_batched")
 
 

@@ -81,3 +81,27 @@ def grad_scale_terms(x, eps=1.0, sigma=1.0):
     np.fill_diagonal(r2, np.inf)
     cn = 24.0 * eps * (2 * s6 * s6 + s6) / r2
     return float(np.linalg.norm((cn[:, :, None] * np.abs(d)).sum(1)))
+
+
+def morse_bounds(x, eps=1.0, re=1.0, rho=6.0, u=2.0 ** -24):
+    """Error bounds of a Morse evaluation whose pair terms carry relative
+    rounding u: per pair the exponent x = rho (1 - r/re) is off by about
+    7 rho (r/re) u (r from r^2 and a reciprocal square root) plus |x| u, the
+    FP32 exponential adds 2 + 1.2 |x| ulp (CUDA's __expf bound), and the
+    products a few u more, so the pair energy e (e - 2) is off by at most
+    amp u e (e + 2) with amp = 8 + 5 |x| + 14 rho r / re, and the pair vector
+    e (e - 1) d / r alike.  Returns (energy bound, per-coordinate gradient
+    bounds), each twice the sum of those terms (no cancellation assumed)."""
+    p = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    d = p[:, None, :] - p[None, :, :]
+    r = np.sqrt((d ** 2).sum(-1))
+    iu = np.triu_indices(len(p), 1)
+    off = ~np.eye(len(p), dtype=bool)
+    xx = rho * (1.0 - r / re)
+    ex = np.exp(np.where(off, xx, 0.0))
+    amp = 8.0 + 5.0 * np.abs(xx) + 14.0 * rho * r / re
+    e_bound = 2.0 * u * eps * (amp * ex * (ex + 2.0))[iu].sum()
+    rs = np.where(off, r, 1.0)
+    c = np.where(off, amp * (2.0 * eps * rho / re) * ex * (ex + 1.0) / rs, 0.0)
+    g_bound = 2.0 * u * (c[:, :, None] * np.abs(d)).sum(1)
+    return float(e_bound), g_bound.reshape(-1)

@@ -66,3 +66,37 @@ def test_null_ctx_is_rejected(lib):
     assert lib.lj_ctx_get_tuning(None, 0, None) == -1
     lib.lj_ctx_autotune_bh.restype = ctypes.c_int
     assert lib.lj_ctx_autotune_bh(None, None, None, None, None) == -1
+    lib.lj_energy_grad_batched_pot.restype = ctypes.c_int
+    assert lib.lj_energy_grad_batched_pot(None, None, 0, 0, None, None, None, 1,
+                                          ctypes.c_double(1.0), ctypes.c_double(1.0),
+                                          ctypes.c_double(6.0), None) == -1
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the C struct's size and field
+    offsets (a C program built against include/lj_bh.h prints them)."""
+    import subprocess
+    from paper_2510_25938_gb300 import lj_bh as L
+    pairs = {"lj_batch": L._Batch, "lj_lbfgs_params": L._Lbfgs, "lj_bh_params": L._Bh,
+             "lj_bh_state": L._State, "lj_bh_trace": L._Trace, "lj_tuning": L._Tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lj_bh.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
