@@ -55,11 +55,9 @@ __host__ __device__ constexpr size_t bhc_head_bytes(int n_atoms) {
 // Measured on LJ38, 64 walkers x K = 8: 23.9 against 25.9 ms per 10-step
 // launch.  At 255 registers 4 CTAs of 64 threads fit on an SM (608 on 152
 // SMs, more than the 512 CTAs of that workload).
-// POT: pair potential (LJ_POT_LJ, Eq. (1); LJ_POT_MORSE, with no half-pair
-// buffer: its evaluations are one-sided rows).
+// POT: pair potential (LJ_POT_LJ, Eq. (1); LJ_POT_MORSE).
 template <int T, int A, bool MIXED, int POT = LJ_POT_LJ>
 __global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhArgs a) {
-  constexpr bool kHalf = POT == LJ_POT_LJ;
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int n = a.n_atoms;
@@ -84,7 +82,7 @@ __global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhA
   void* hbuf;
   void* hist;
   long long* word;
-  carve_team<T>(sp, n, kHalf, a.hist_on_chip ? a.hist_slot_bytes : 0, pos, hbuf, hist, tm.red,
+  carve_team<T>(sp, n, true, a.hist_on_chip ? a.hist_slot_bytes : 0, pos, hbuf, hist, tm.red,
                 word);
   MinParams p = to_dev(a.p);
   // hbuf: pair buffer up to 64 atoms, tile accumulators above 256; with
@@ -238,17 +236,16 @@ __global__ void __launch_bounds__(T, T <= 64 ? 3 : 0) bh_cluster_kernel(ljh::BhA
 
 template <int T, int A, bool MIXED, int POT>
 cudaError_t plan_one(int n_atoms, int m, int n_walkers, int K, ljh::Plan* out, bool hist_global) {
-  constexpr bool kHalf = POT == LJ_POT_LJ;
   out->slot_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
   out->team = T;
   if (K <= LJ_MAX_K) {                // one cluster of K CTAs per walker
     const bool on_chip = !hist_global && bhc_head_bytes<T>(n_atoms) +
-                                             team_smem_bytes<T>(n_atoms, kHalf, out->slot_bytes) <=
+                                             team_smem_bytes<T>(n_atoms, true, out->slot_bytes) <=
                                          kSmemBudget;
     out->hist_on_chip = on_chip ? 1 : 0;
     out->slots = on_chip ? 0 : (int64_t)n_walkers * K;
     const size_t smem = bhc_head_bytes<T>(n_atoms) +
-                        team_smem_bytes<T>(n_atoms, kHalf, on_chip ? out->slot_bytes : 0);
+                        team_smem_bytes<T>(n_atoms, true, on_chip ? out->slot_bytes : 0);
     auto k = bh_cluster_kernel<T, A, MIXED, POT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -619,13 +619,29 @@ __device__ __forceinline__ void pair_term_f64(const PosD& a, const PosD& b, doub
   vx = c * dx; vy = c * dy; vz = c * dz;
 }
 
+// |d|^2 of a double-float vector with one renormalisation: the high squares
+// exactly (TwoProd by FMA), summed by two TwoSums, and every low-order part
+// (their rounding errors, 2 hi lo, the TwoProd errors) gathered in one FP32
+// word.  Dropped: lo^2 and the roundings of the low word, ~2^-47 relative.
+__device__ __forceinline__ ff df_norm2(ff x, ff y, ff z) {
+  const float px = __fmul_rn(x.hi, x.hi), py = __fmul_rn(y.hi, y.hi), pz = __fmul_rn(z.hi, z.hi);
+  const float ex = fmaf(x.hi, x.hi, -px), ey = fmaf(y.hi, y.hi, -py), ez = fmaf(z.hi, z.hi, -pz);
+  const ff s1 = ff_two_sum(px, py);
+  const ff s2 = ff_two_sum(s1.hi, pz);
+  float lo = __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(__fadd_rn(ex, ey), ez));
+  lo = fmaf(__fadd_rn(x.hi, x.hi), x.lo, lo);
+  lo = fmaf(__fadd_rn(y.hi, y.hi), y.lo, lo);
+  lo = fmaf(__fadd_rn(z.hi, z.hi), z.lo, lo);
+  return df_fast_two_sum(s2.hi, lo);
+}
+
 // pair term in double-float on coordinates scaled by 1/sigma
 __device__ __forceinline__ void pair_term_df(const PosDF& a, const PosDF& b, ff& vx, ff& vy,
                                              ff& vz, ff& e) {
   const ff dx = df_sub(ff{a.xh, a.xl}, ff{b.xh, b.xl});
   const ff dy = df_sub(ff{a.yh, a.yl}, ff{b.yh, b.yl});
   const ff dz = df_sub(ff{a.zh, a.zl}, ff{b.zh, b.zl});
-  const ff r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  const ff r2 = df_norm2(dx, dy, dz);
   const ff s2 = df_rcp(r2);
   const ff s6 = df_mul(df_sqr(s2), s2);
   const ff t = df_add_f(s6, -1.f);

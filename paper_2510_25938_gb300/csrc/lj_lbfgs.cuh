@@ -26,12 +26,10 @@ __device__ __forceinline__ MinParams to_dev(const ljh::MinParamsH& h) {
 // Register budget: teams for more than 256 atoms (which carry the tiled
 // double-float evaluation) are allowed all registers of one CTA per SM; the
 // others are left to the compiler's own occupancy choice.
-// POT: pair potential (LJ_POT_LJ, Eq. (1); LJ_POT_MORSE).  Morse teams keep
-// no half-pair buffer (their evaluations are one-sided rows).
+// POT: pair potential (LJ_POT_LJ, Eq. (1); LJ_POT_MORSE).
 template <int T, int A, bool MIXED, int POT = LJ_POT_LJ>
 __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
     lbfgs_kernel(ljh::LbfgsArgs a) {
-  constexpr bool kHalf = POT == LJ_POT_LJ;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int TPC = cta_threads_for(T) / T;
   const int team = threadIdx.x / T;
@@ -43,7 +41,7 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
   void* hbuf;
   void* hist;
   const size_t hb = a.hist_on_chip ? a.hist_slot_bytes : 0;
-  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, kHalf, hb), a.max_n, kHalf, hb, pos,
+  carve_team<T>(smem + team * team_smem_bytes<T>(a.max_n, true, hb), a.max_n, true, hb, pos,
                 hbuf, hist, tm.red, word);
   MinParams p = to_dev(a.p);
   // hbuf: pair buffer up to 64 atoms, tile accumulators above 256.  With
@@ -140,13 +138,12 @@ __global__ void __launch_bounds__(cta_threads_for(T), T * A > 256 ? 1 : 0)
 template <int T, int A, bool MIXED, int POT>
 cudaError_t plan_one(int max_n, int m, int64_t n_cand, int device, ljh::Plan* out,
                      bool hist_global) {
-  constexpr bool kHalf = POT == LJ_POT_LJ;
   constexpr int threads = cta_threads_for(T);
   constexpr int TPC = threads / T;
   const size_t hist_bytes = align16(2 * (size_t)m * A * 3 * T * (MIXED ? sizeof(float) : sizeof(double)));
   const bool on_chip =
-      !hist_global && TPC * team_smem_bytes<T>(max_n, kHalf, hist_bytes) <= kSmemBudget;
-  const size_t smem = TPC * team_smem_bytes<T>(max_n, kHalf, on_chip ? hist_bytes : 0);
+      !hist_global && TPC * team_smem_bytes<T>(max_n, true, hist_bytes) <= kSmemBudget;
+  const size_t smem = TPC * team_smem_bytes<T>(max_n, true, on_chip ? hist_bytes : 0);
   auto k = lbfgs_kernel<T, A, MIXED, POT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -136,14 +136,29 @@ __device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
 // E = (eps / 2) sum_i sum_{j != i} e (e - 2), and
 // g_i = -(2 eps rho / re) sum_{j != i} e (e - 1) (x_i - x_j) / r.
 // FP32 (first tier of the mixed path; compensated energy) and FP64; the
-// mixed path has no double-float tier for this potential.  Coincident atoms
-// give E = +inf (and a non-finite gradient), as for Eq. (1).
+// mixed path has no double-float tier for this potential.  FP64 teams with
+// a half-pair buffer (clusters of up to 64 atoms) take each pair once, as
+// for Eq. (1): pair p's vector e (e - 1) (x_i - x_j) / r goes to the buffer,
+// then every (atom, component) row is summed, +v over j > i, -v over j < i.
+// Coincident atoms give E = +inf (and a non-finite gradient), as for Eq. (1).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void pair_term_morse_f64(const PosD& a, const PosD& b, double rho,
+                                                    double rr, double& vx, double& vy,
+                                                    double& vz, double& e) {
+  const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  const double r = sqrt(r2);
+  const double ex = exp(fma(-rr, r, rho));
+  e = r2 > 0.0 ? ex * (ex - 2.0) : __longlong_as_double(0x7ff0000000000000LL);
+  const double c = ex * (ex - 1.0) / r;
+  vx = c * dx; vy = c * dy; vz = c * dz;
+}
+
 template <int T, int A, typename P>
 __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
                                                const typename P::XP (&x)[A][3],
                                                typename P::XG (&g)[A][3], void* posv,
-                                               const MinParams& p,
+                                               void* hbuf, const MinParams& p,
                                                const typename P::V (*d)[3],
                                                typename P::F& E, typename P::S& dphi) {
   using X = typename P::XP;
@@ -211,6 +226,72 @@ __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
       }
     }
     E = ff_scale(team_sum_ff<T>(tm, e), p.k.m_half_f);
+  } else if (hbuf != nullptr && !p.tiled) {
+    // ---- half-pair FP64 evaluation (pair phase, then row sums) -------------
+    const int np = n_pairs(n);
+    const PosD* pos = static_cast<const PosD*>(posv);
+    double* vb = static_cast<double*>(hbuf);
+    double* gsum = static_cast<double*>(posv);
+    const double rho = p.k.rho, rr = p.k.rho_re;
+    int i1, j1, i2, j2;
+    pair_start(n, tm.rank, i1, j1);
+    i2 = i1; j2 = j1;
+    pair_advance(n, T, i2, j2);
+    dd e{0.0, 0.0};
+    for (int q = tm.rank; q < np; q += 2 * T) {
+      const bool two = q + T < np;
+      const int ib = two ? i2 : 0, jb = two ? j2 : 1;
+      double ax, ay, az, ae, bx, by, bz, be;
+      pair_term_morse_f64(pos[i1], pos[j1], rho, rr, ax, ay, az, ae);
+      pair_term_morse_f64(pos[ib], pos[jb], rho, rr, bx, by, bz, be);
+      vb[q] = ax; vb[np + q] = ay; vb[2 * np + q] = az;
+      double eb = ae;
+      if (two) {
+        vb[q + T] = bx; vb[np + q + T] = by; vb[2 * np + q + T] = bz;
+        eb += be;
+      }
+      const dd t = dd_two_sum(e.hi, eb);    // compensated energy sum
+      e.hi = t.hi;
+      e.lo = __dadd_rn(e.lo, t.lo);
+      pair_advance(n, 2 * T, i1, j1);
+      pair_advance(n, 2 * T, i2, j2);
+    }
+    tm.sync();
+    const double gs = p.k.m_g;
+    for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
+      const int ii = q3 / 3;
+      const double* vc = vb + (q3 - 3 * ii) * np;
+      const int ri = row_base(n, ii);       // all lanes walk j together
+      int rj = -1;
+      double sacc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j0 = 0; j0 < n; j0 += 4) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          const int qq = j < ii ? rj + ii : ri + j;
+          v[u] = 0.0;
+          if (j < n && j != ii) v[u] = vc[qq];
+          if (j < ii) v[u] = -v[u];
+          rj += n - j - 2;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sacc[u] += v[u];
+      }
+      gsum[q3] = -gs * ((sacc[0] + sacc[1]) + (sacc[2] + sacc[3]));
+    }
+    tm.sync();
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int ii = tm.rank + a * T;
+      if (ii < n) {
+        g[a][0] = gsum[3 * ii]; g[a][1] = gsum[3 * ii + 1]; g[a][2] = gsum[3 * ii + 2];
+      } else {
+        g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    E = team_sum_dd<T>(tm, e) * p.k.eps;
   } else {
     const double rho = p.k.rho, rr = p.k.rho_re, gsc = p.k.m_g;
     const double kInf = __longlong_as_double(0x7ff0000000000000LL);
@@ -269,7 +350,7 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   using S = typename P::S;
   constexpr int PM = P::PM;
   if constexpr (P::POT != LJ_POT_LJ) {
-    evaluate_morse<T, A, P>(tm, n, x, g, posv, p, d, E, dphi);
+    evaluate_morse<T, A, P>(tm, n, x, g, posv, hbuf, p, d, E, dphi);
     return;
   }
   tm.sync();  // previous readers of pos are done
@@ -322,10 +403,17 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           pair_term_df(pos[i1], pos[j1], ax, ay, az, ae);
           pair_term_df(pos[ib], pos[jb], bx, by, bz, be);
           vb[q] = ax; vb[np + q] = ay; vb[2 * np + q] = az;
-          e = df_add(e, ae);
+          // cascaded TwoSum (Ogita, Rump and Oishi 2005, Sum2): the high
+          // word's chain is one add; every rounding error and low word goes
+          // to e.lo
+          ff t = ff_two_sum(e.hi, ae.hi);
+          e.hi = t.hi;
+          e.lo = __fadd_rn(e.lo, __fadd_rn(t.lo, ae.lo));
           if (two) {
             vb[q + T] = bx; vb[np + q + T] = by; vb[2 * np + q + T] = bz;
-            e = df_add(e, be);
+            t = ff_two_sum(e.hi, be.hi);
+            e.hi = t.hi;
+            e.lo = __fadd_rn(e.lo, __fadd_rn(t.lo, be.lo));
           }
           pair_advance(n, 2 * T, i1, j1);
           pair_advance(n, 2 * T, i2, j2);
@@ -336,7 +424,8 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
           const int ii = q3 / 3;
           const ff* vc = vb + (q3 - 3 * ii) * np;
           // All lanes walk j = 0 .. n-1 together (no divergence), four
-          // independent sums, loads issued a block of four ahead of the adds.
+          // independent cascaded-TwoSum sums (Sum2, as for the energy),
+          // loads issued a block of four ahead of the adds.
           const int ri = row_base(n, ii);
           int rj = -1;                          // row_base(n, j)
           ff s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -352,7 +441,11 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
               rj += n - j - 2;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s[u] = df_add(s[u], v[u]);
+            for (int u = 0; u < 4; ++u) {
+              const ff t = ff_two_sum(s[u].hi, v[u].hi);
+              s[u].hi = t.hi;
+              s[u].lo = __fadd_rn(s[u].lo, __fadd_rn(t.lo, v[u].lo));
+            }
           }
           const ff sum = df_add(df_add(s[0], s[1]), df_add(s[2], s[3]));
           gsum[q3] = -gs * (sum.hi + sum.lo);
