@@ -539,6 +539,31 @@ __device__ __forceinline__ ff df_from_double(double x) {
 }
 __device__ __forceinline__ double df_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// |d|^2 of a double-float vector with one renormalisation: the high squares
+// exactly (TwoProd by FMA), summed by two TwoSums, and every low-order part
+// (their rounding errors, 2 hi lo, the TwoProd errors) gathered in one FP32
+// word.  Dropped: lo^2 and the roundings of the low word, ~2^-47 relative.
+__device__ __forceinline__ ff df_norm2(ff x, ff y, ff z) {
+  const float px = __fmul_rn(x.hi, x.hi), py = __fmul_rn(y.hi, y.hi), pz = __fmul_rn(z.hi, z.hi);
+  const float ex = fmaf(x.hi, x.hi, -px), ey = fmaf(y.hi, y.hi, -py), ez = fmaf(z.hi, z.hi, -pz);
+  const ff s1 = ff_two_sum(px, py);
+  const ff s2 = ff_two_sum(s1.hi, pz);
+  float lo = __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(__fadd_rn(ex, ey), ez));
+  lo = fmaf(__fadd_rn(x.hi, x.hi), x.lo, lo);
+  lo = fmaf(__fadd_rn(y.hi, y.hi), y.lo, lo);
+  lo = fmaf(__fadd_rn(z.hi, z.hi), z.lo, lo);
+  return df_fast_two_sum(s2.hi, lo);
+}
+
+// s += v for a running double-float sum: TwoSum of the high words, every
+// rounding error and low word gathered in s.lo (Ogita, Rump and Oishi 2005,
+// Sum2); s.lo is renormalised where the sum is stored
+__device__ __forceinline__ void df_acc(ff& s, ff v) {
+  const ff t = ff_two_sum(s.hi, v.hi);
+  s.hi = t.hi;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, v.lo));
+}
+
 // One row of the pair sum in df arithmetic, coordinates pre-scaled by
 // 1/sigma (so s2 = 1/r^2).  Accumulates acc_i = sum_j s2 s6 (2 s6 - 1) d_ij
 // and e_i = sum_j s6 (s6 - 1), both as df.
@@ -552,16 +577,16 @@ __device__ __forceinline__ void pair_row_df(int n, int i, ff px, ff py, ff pz,
     const ff dx = df_sub(px, ff{q.xh, q.xl});
     const ff dy = df_sub(py, ff{q.yh, q.yl});
     const ff dz = df_sub(pz, ff{q.zh, q.zl});
-    const ff r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+    const ff r2 = df_norm2(dx, dy, dz);
     ff s2 = df_rcp(r2);
     if (j == i) s2 = ff{0.f, 0.f};
     const ff s6 = df_mul(df_sqr(s2), s2);
     const ff t = df_add_f(s6, -1.f);
-    e = df_add(e, df_mul(s6, t));
+    df_acc(e, df_mul(s6, t));
     const ff c = df_mul(df_mul(s2, s6), df_add(s6, t));
-    ax = df_add(ax, df_mul(c, dx));
-    ay = df_add(ay, df_mul(c, dy));
-    az = df_add(az, df_mul(c, dz));
+    df_acc(ax, df_mul(c, dx));
+    df_acc(ay, df_mul(c, dy));
+    df_acc(az, df_mul(c, dz));
   }
 }
 
@@ -617,22 +642,6 @@ __device__ __forceinline__ void pair_term_f64(const PosD& a, const PosD& b, doub
   e = s6 * t;
   const double c = (s2 * s6) * (s6 + t);
   vx = c * dx; vy = c * dy; vz = c * dz;
-}
-
-// |d|^2 of a double-float vector with one renormalisation: the high squares
-// exactly (TwoProd by FMA), summed by two TwoSums, and every low-order part
-// (their rounding errors, 2 hi lo, the TwoProd errors) gathered in one FP32
-// word.  Dropped: lo^2 and the roundings of the low word, ~2^-47 relative.
-__device__ __forceinline__ ff df_norm2(ff x, ff y, ff z) {
-  const float px = __fmul_rn(x.hi, x.hi), py = __fmul_rn(y.hi, y.hi), pz = __fmul_rn(z.hi, z.hi);
-  const float ex = fmaf(x.hi, x.hi, -px), ey = fmaf(y.hi, y.hi, -py), ez = fmaf(z.hi, z.hi, -pz);
-  const ff s1 = ff_two_sum(px, py);
-  const ff s2 = ff_two_sum(s1.hi, pz);
-  float lo = __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(__fadd_rn(ex, ey), ez));
-  lo = fmaf(__fadd_rn(x.hi, x.hi), x.lo, lo);
-  lo = fmaf(__fadd_rn(y.hi, y.hi), y.lo, lo);
-  lo = fmaf(__fadd_rn(z.hi, z.hi), z.lo, lo);
-  return df_fast_two_sum(s2.hi, lo);
 }
 
 // pair term in double-float on coordinates scaled by 1/sigma
@@ -706,10 +715,11 @@ __device__ void df_tile_eval(const Team<T>& tm, int n, const PosDF* __restrict__
       if (__any_sync(kFull, act)) {
         ff vx, vy, vz, ep;
         pair_term_df(pi, pj, vx, vy, vz, ep);
-        if (act) {
-          fx = df_add(fx, vx); fy = df_add(fy, vy); fz = df_add(fz, vz);
-          hx = df_sub(hx, vx); hy = df_sub(hy, vy); hz = df_sub(hz, vz);
-          e = df_add(e, ep);
+        if (act) {   // cascaded TwoSum (Sum2): one add on each high word's chain
+          df_acc(fx, vx); df_acc(fy, vy); df_acc(fz, vz);
+          df_acc(hx, ff{-vx.hi, -vx.lo}); df_acc(hy, ff{-vy.hi, -vy.lo});
+          df_acc(hz, ff{-vz.hi, -vz.lo});
+          df_acc(e, ep);
         }
       }
       pj = shfl_pos(pj, src);
