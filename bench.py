@@ -96,7 +96,8 @@ def parse():
                     help="run only the evaluation microbench and print its JSON")
     ap.add_argument("--micro-repeats", type=int, default=100)
     ap.add_argument("--no-tune", action="store_true",
-                    help="skip lj_ctx_autotune_bh: library default team and history placement, "
+                    help="skip the autotuner (lj_ctx_autotune_bh, or lj_ctx_autotune for the "
+                         "batched workloads): library default team and history placement, "
                          "switch_gtol 1e-4")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline, FP64 path and e2e only (no error, K-sweep, search-quality "
@@ -437,17 +438,25 @@ def batch_cpu_baseline(name, x0, off, uniform, budget_s):
             "sample": f"first {done} of {n_total} candidates ({conv} converged) in {dt:.1f} s"}
 
 
-def time_batch(L, ctx, name, prec, x0, off, uniform, reps, warmup, flush, graph):
-    """Batched minimisation of one workload, autotuned, timed with CUDA events
-    around each call (or each replay of one captured CUDA graph of the call),
-    inputs resident and L2 flushed before each timed call."""
+# switch_gtol the autotuner picks for the fcc-fragment workloads (and the
+# value the batched workloads use when run without the autotuner)
+BATCH_SWITCH_GTOL_UNTUNED = 1e-4
+
+
+def time_batch(L, ctx, name, prec, x0, off, uniform, reps, warmup, flush, graph, tune=True):
+    """Batched minimisation of one workload, autotuned (unless tune is False:
+    default team sizes, switch_gtol 1e-4), timed with CUDA events around each
+    call (or each replay of one captured CUDA graph of the call), inputs
+    resident and L2 flushed before each timed call."""
     import torch
     w = BATCH_WORKLOADS[name]
     dev = torch.device("cuda", torch.cuda.current_device())
     n_cand = w["n_cand"]
     xin = torch.as_tensor(x0, dtype=torch.float64, device=dev).contiguous()
     offd = torch.as_tensor(off, device=dev) if off is not None else None
-    if offd is None:
+    if not tune:
+        tuned = None
+    elif offd is None:
         tuned = ctx.autotune_batch(xin, n_cand, uniform, w["m"], prec, max_sample=n_cand // 4)
     else:
         tuned = ctx.autotune(w["n_hi"], w["m"], prec)
@@ -457,7 +466,8 @@ def time_batch(L, ctx, name, prec, x0, off, uniform, reps, warmup, flush, graph)
     st = torch.empty(n_cand, dtype=torch.int32, device=dev)
     stats = L.new_stats(dev)
     kw = dict(atom_offset=offd, max_n=w["n_hi"]) if offd is not None else dict(uniform_n=uniform)
-    p = L.LbfgsParams(prec=prec, m=w["m"])
+    p = L.LbfgsParams(prec=prec, m=w["m"],
+                      switch_gtol=0.0 if tune else BATCH_SWITCH_GTOL_UNTUNED)
 
     def call():
         L.lbfgs_minimize_batched(ctx, x, e, st, None, None, stats, n_cand=n_cand, params=p, **kw)
@@ -510,7 +520,7 @@ def time_batch(L, ctx, name, prec, x0, off, uniform, reps, warmup, flush, graph)
     return out
 
 
-def batch_workload_record(L, name, flush, reps, warmup, cpu_budget):
+def batch_workload_record(L, name, flush, reps, warmup, cpu_budget, tune=True):
     w = BATCH_WORKLOADS[name]
     x0, off, uniform = batch_inputs(name)
     rec = {"workload": w["desc"]}
@@ -518,7 +528,7 @@ def batch_workload_record(L, name, flush, reps, warmup, cpu_budget):
         ctx = L.Ctx()
         rec[pname] = time_batch(L, ctx, name, prec, x0, off, uniform,
                                 reps if pname == "mixed" else max(1, reps // 2), warmup, flush,
-                                graph=(off is not None))
+                                graph=(off is not None), tune=tune)
         ctx.close()
     rec["value"] = rec["mixed"]["value"]
     rec["mixed_over_fp64"] = rec["mixed"]["value"] / max(rec["fp64"]["value"], 1e-30)
@@ -537,7 +547,7 @@ def run_batch_workload(args):
     torch.cuda.set_device(0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     rec = batch_workload_record(L, args.workload, flush, args.steps, args.warmup,
-                                0.0 if args.no_cpu_baseline else 10.0)
+                                0.0 if args.no_cpu_baseline else 10.0, tune=not args.no_tune)
     line = {"metric": "converged LJ minimisations/s", "value": rec["value"],
             "unit": "converged minimisations/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64",

@@ -750,4 +750,83 @@ __device__ void df_tile_eval(const Team<T>& tm, int n, const PosDF* __restrict__
   tm.sync();
 }
 
+// FP64 twin of df_tile_eval (clusters above 256 atoms, same circle-method
+// rounds of 32 x 32 tiles): pair terms by pair_term_f64 on unscaled
+// coordinates, per-atom FP64 accumulators acc[c * n + atom] in the same
+// 24-byte-per-atom slot; a lane's pair energies are summed over its tile,
+// then added into e with TwoSum.  Each pair once: the FP64 pipe, which bounds
+// these evaluations, does ~40% fewer operations than for two one-sided terms.
+__device__ __forceinline__ void shfl_posd(PosD& q, int src) {
+  q.x = __shfl_sync(kFull, q.x, src);
+  q.y = __shfl_sync(kFull, q.y, src);
+  q.z = __shfl_sync(kFull, q.z, src);
+}
+
+template <int T>
+__device__ void d_tile_eval(const Team<T>& tm, int n, const PosD* __restrict__ pos, double sig2,
+                            double* acc, dd& e) {
+  constexpr int W = T / 32;
+  const int lane = tm.rank & 31, warp = tm.rank >> 5;
+  for (int i = tm.rank; i < 3 * n; i += T) acc[i] = 0.0;
+  tm.sync();
+  const int nb = (n + 31) >> 5;
+  const int nbe = nb + (nb & 1);
+  const PosD far{0x1p300, 0x1p300, 0x1p300, 0.0};
+  auto tile = [&](int I, int J) {
+    const bool diag = I == J;
+    const int i = 32 * I + lane;
+    const bool vi = i < n;
+    const PosD pi = vi ? pos[i] : far;
+    const int jl = 32 * J + lane;
+    PosD pj = jl < n ? pos[jl] : far;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    double hx = 0.0, hy = 0.0, hz = 0.0;   // reaction of the rotating J atom
+    double eb = 0.0;
+    const int src = (lane + 1) & 31;
+    for (int k = 0; k < 32; ++k) {
+      const int jk = 32 * J + ((lane + k) & 31);
+      bool act = vi && jk < n;
+      if (diag) act = act && k >= 1 && (k < 16 || (k == 16 && lane < 16));
+      if (__any_sync(kFull, act)) {
+        double vx, vy, vz, ep;
+        pair_term_f64(pi, pj, sig2, vx, vy, vz, ep);
+        if (act) {
+          fx += vx; fy += vy; fz += vz;
+          hx -= vx; hy -= vy; hz -= vz;
+          eb += ep;
+        }
+      }
+      shfl_posd(pj, src);
+      hx = __shfl_sync(kFull, hx, src);
+      hy = __shfl_sync(kFull, hy, src);
+      hz = __shfl_sync(kFull, hz, src);
+    }
+    const dd t = dd_two_sum(e.hi, eb);
+    e.hi = t.hi;
+    e.lo = __dadd_rn(e.lo, t.lo);
+    if (diag) {
+      fx += hx; fy += hy; fz += hz;
+    } else if (jl < n) {
+      acc[jl] += hx;
+      acc[n + jl] += hy;
+      acc[2 * n + jl] += hz;
+    }
+    if (vi) {
+      acc[i] += fx;
+      acc[n + i] += fy;
+      acc[2 * n + i] += fz;
+    }
+  };
+  for (int r = 0; r < nbe - 1; ++r) {
+    for (int t = warp; t < nbe / 2; t += W) {
+      const int I = t == 0 ? nbe - 1 : (r + t) % (nbe - 1);
+      const int J = t == 0 ? r : (r - t + nbe - 1) % (nbe - 1);
+      if (I < nb && J < nb) tile(I, J);
+    }
+    tm.sync();
+  }
+  for (int b = warp; b < nb; b += W) tile(b, b);
+  tm.sync();
+}
+
 }  // namespace ljd

@@ -617,6 +617,28 @@ __device__ __forceinline__ void evaluate(const Team<T>& tm, int n,
   } else {
     const PosD* pos = static_cast<const PosD*>(posv);
     dd e{0.0, 0.0};
+    // ---- tiled FP64 evaluation (teams for more than 256 atoms) -------------
+    if constexpr (T * A > 256) {
+    if (hbuf != nullptr && p.tiled) {
+      double* acc = static_cast<double*>(hbuf);
+      d_tile_eval<T>(tm, n, pos, p.k.sig2, acc, e);
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const int i = tm.rank + a * T;
+        if (i < n) {
+          g[a][0] = -p.k.gscale * acc[i];
+          g[a][1] = -p.k.gscale * acc[n + i];
+          g[a][2] = -p.k.gscale * acc[2 * n + i];
+        } else {
+          g[a][0] = 0.0; g[a][1] = 0.0; g[a][2] = 0.0;
+        }
+        if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+      }
+      E = team_sum_dd<T>(tm, e) * p.k.e4;
+      if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+      return;
+    }
+    }
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int i = tm.rank + a * T;
