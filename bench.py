@@ -687,16 +687,17 @@ def morse_bh_record(L, flush, reps, warmup, cpu_budget):
                 times.append(ev0.elapsed_time(ev1) / 1e3)
         t = sum(times)
         sd = L.stats_dict(stats)
-        fl = MORSE_PAIR_FLOPS * (sd["pairs32"] + sd["pairs64"]) + 8.0 * (
+        fl = MORSE_PAIR_FLOPS * (sd["pairs32"] + sd["pairs64"] + sd["pairs_df"]) + 8.0 * (
             sd["vec_elems32"] + sd["vec_elems64"]) + 12.0 * 3 * N_ATOMS * (
             sd["iters32"] + sd["iters64"])
         out[pname] = {"value": sd["converged"] / t, "unit": "converged minimisations/s",
                       "ms_per_launch": 1e3 * t / len(times), "launches": len(times),
                       "converged_fraction": sd["converged"] / max(sd["minimisations"], 1),
                       "achieved_tflops": fl / t / 1e12,
-                      "fp64_pair_share": sd["pairs64"] / max(sd["pairs32"] + sd["pairs64"], 1),
+                      "fp64_pair_share": sd["pairs64"] / max(
+                          sd["pairs32"] + sd["pairs64"] + sd["pairs_df"], 1),
                       "per_minimisation": {k: sd[k] / max(sd["minimisations"], 1) for k in (
-                          "evals32", "evals64", "iters32", "iters64")}}
+                          "evals32", "evals_df", "evals64", "iters32", "iters64")}}
     ctx.close()
     out["value"] = out["mixed"]["value"]
     out["mixed_over_fp64"] = out["mixed"]["value"] / max(out["fp64"]["value"], 1e-30)

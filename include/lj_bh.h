@@ -71,10 +71,13 @@ typedef enum { LJ_F32 = 0, LJ_F64 = 1 } lj_dtype;
  *   LJ_POT_LJ     Eq. (1): E = 4 eps sum_{i<j} [(sigma/r)^12 - (sigma/r)^6].
  *   LJ_POT_MORSE  Morse (Morse 1929, the form used for clusters):
  *                 E = eps sum_{i<j} e_ij (e_ij - 2), e_ij = exp(rho (1 - r_ij / re)),
- *                 with re passed in the sigma slot and rho > 0 its range
- *                 (rho = 6 has the width of the LJ well).  Coincident atoms give a
- *                 non-finite energy, as for Eq. (1).  The MIXED minimiser runs its
- *                 FP32 tier and then FP64 (no double-float tier for this potential). */
+ *                 with re passed in the sigma slot and 0 < rho <= 64 its range
+ *                 (rho = 6 has the width of the LJ well; the bound keeps e^rho
+ *                 inside FP32's range).  Coincident atoms give a non-finite
+ *                 energy, as for Eq. (1).  The MIXED minimiser's three tiers are
+ *                 those of Eq. (1); its double-float tier forms e^x with a
+ *                 double-float exponential (argument reduction by ln 2 and a
+ *                 Taylor polynomial, ~2^-42 relative). */
 typedef enum { LJ_POT_LJ = 0, LJ_POT_MORSE = 1 } lj_potential;
 
 typedef enum {
@@ -265,7 +268,7 @@ lj_status lj_energy_grad_batched(lj_ctx* ctx, const lj_batch* batch, lj_precisio
  * e (e - 1) (x_i - x_j) / r_ij.  Morse clusters run one team per candidate
  * in one-sided rows, FP32 (FP32 exp and reciprocal square root,
  * compensated energy) or FP64.  Errors as lj_energy_grad_batched, plus
- * INVALID_ARG for an unknown potential or rho <= 0 (Morse).
+ * INVALID_ARG for an unknown potential or rho outside (0, 64] (Morse).
  */
 lj_status lj_energy_grad_batched_pot(lj_ctx* ctx, const lj_batch* batch, lj_precision prec,
                                      lj_dtype xtype, const void* d_x, double* d_energy,

@@ -146,8 +146,8 @@ lj_status check_batch(lj_ctx* ctx, const lj_batch* b, int* max_n) {
 lj_status check_pot(lj_ctx* ctx, int32_t potential, double rho) {
   if (potential != LJ_POT_LJ && potential != LJ_POT_MORSE)
     return fail(ctx, LJ_ERR_INVALID_ARG, "unknown pair potential");
-  if (potential == LJ_POT_MORSE && !(rho > 0.0 && std::isfinite(rho)))
-    return fail(ctx, LJ_ERR_INVALID_ARG, "Morse rho must be finite and > 0");
+  if (potential == LJ_POT_MORSE && !(rho > 0.0 && rho <= 64.0))
+    return fail(ctx, LJ_ERR_INVALID_ARG, "Morse rho must be in (0, 64]");
   return LJ_OK;
 }
 

@@ -26,6 +26,8 @@ struct LjConsts {
   double m_g;           // 2 eps rho / re: gradient factor
   double m_half;        // eps / 2: energy factor of a one-sided sum
   float rho_f, rho_re_f, m_g_f, m_half_f;
+  float rho_lo;         // rho - rho_f: rho as a double-float (rho_f, rho_lo)
+  float eps_f;          // eps: energy factor of a half-pair sum
 };
 
 inline LjConsts make_consts(double eps, double sigma, int pot = 0, double rho = 0.0) {
@@ -54,6 +56,8 @@ inline LjConsts make_consts(double eps, double sigma, int pot = 0, double rho = 
   k.rho_re_f = (float)k.rho_re;
   k.m_g_f = (float)k.m_g;
   k.m_half_f = (float)k.m_half;
+  k.rho_lo = (float)(rho - (double)k.rho_f);
+  k.eps_f = (float)eps;
   return k;
 }
 

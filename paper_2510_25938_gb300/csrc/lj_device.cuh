@@ -564,6 +564,76 @@ __device__ __forceinline__ void df_acc(ff& s, ff v) {
   s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, v.lo));
 }
 
+// sqrt(a) in double-float (Karp and Markstein, ACM TOMS 1997): y ~ 1/sqrt(a)
+// in FP32, s = a y, and one correction s + y (a - s^2) / 2 with a - s^2
+// formed exactly (TwoProd); ~2^-46 relative.  a = 0 gives 0.
+__device__ __forceinline__ ff df_sqrt(ff a) {
+  if (!(a.hi > 0.f)) return ff{0.f, 0.f};
+  const float y = rsqrtf(a.hi);
+  const float s = __fmul_rn(a.hi, y);
+  const ff p = df_two_prod(s, s);
+  const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
+  return df_fast_two_sum(s, __fmul_rn(__fmul_rn(res, y), 0.5f));
+}
+
+// e^x in double-float.  Argument reduction x = k ln 2 + r, k = rint(x / ln 2),
+// with ln 2 split into three FP32 words of which the first has 16 bits (so
+// k ln2_1 is exact for |k| < 256); then e^r = (e^(r/32))^32, e^(r/32) by its
+// Taylor series to degree 7 in double-float Horner form (|r/32| <= 0.0109:
+// the first dropped term is below 2^-58), five squarings (which multiply the
+// relative error by 32: ~2^-42 in all), and the exact scaling of both words by
+// 2^k.  For x < -87.3 (e^x below FP32's normal range) the result is 0.
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kLn2_1 = (float)((double)(long long)(kLn2 * 65536.0) / 65536.0);
+constexpr float kLn2_2 = (float)(kLn2 - (double)kLn2_1);
+constexpr float kLn2_3 = (float)(kLn2 - (double)kLn2_1 - (double)kLn2_2);
+// 1/k! as double-float words (high: the FP32 rounding, low: the FP32
+// rounding of the rest), formed at compile time
+constexpr float df_hi(double c) { return (float)c; }
+constexpr float df_lo(double c) { return (float)(c - (double)(float)c); }
+constexpr float kF3h = df_hi(1.0 / 6), kF3l = df_lo(1.0 / 6);
+constexpr float kF4h = df_hi(1.0 / 24), kF4l = df_lo(1.0 / 24);
+constexpr float kF5h = df_hi(1.0 / 120), kF5l = df_lo(1.0 / 120);
+constexpr float kF6h = df_hi(1.0 / 720), kF6l = df_lo(1.0 / 720);
+constexpr float kF7h = df_hi(1.0 / 5040), kF7l = df_lo(1.0 / 5040);
+__device__ __forceinline__ ff df_exp(ff x) {
+  if (x.hi < -87.3f) return ff{0.f, 0.f};
+  const float k = rintf(__fmul_rn(x.hi, 1.44269504f));
+  ff r = df_add_f(x, -__fmul_rn(k, kLn2_1));            // k ln2_1 exact
+  r = df_sub(r, df_two_prod(k, kLn2_2));
+  r = df_add_f(r, -__fmul_rn(k, kLn2_3));
+  r.hi *= 0.03125f;                                      // r / 32, exact
+  r.lo *= 0.03125f;
+  ff p{kF7h, kF7l};
+  p = df_add(df_mul(p, r), ff{kF6h, kF6l});
+  p = df_add(df_mul(p, r), ff{kF5h, kF5l});
+  p = df_add(df_mul(p, r), ff{kF4h, kF4l});
+  p = df_add(df_mul(p, r), ff{kF3h, kF3l});
+  p = df_add(df_mul(p, r), ff{0.5f, 0.f});
+  p = df_add_f(df_mul(p, r), 1.f);
+  p = df_add_f(df_mul(p, r), 1.f);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) p = df_sqr(p);
+  const float sc = __int_as_float(((int)k + 127) << 23);   // 2^k, k in [-126, 127]
+  return ff{p.hi * sc, p.lo * sc};
+}
+
+// Morse pair term in double-float on coordinates scaled by 1/re: with
+// e = exp(rho (1 - r)), v = e (e - 1) (x_i - x_j) / r and e_pair = e (e - 2)
+// (+inf for coincident atoms).  rho is the double-float range parameter.
+__device__ __forceinline__ void pair_term_morse_df(const PosDF& a, const PosDF& b, ff rho,
+                                                   ff& vx, ff& vy, ff& vz, ff& e) {
+  const ff dx = df_sub(ff{a.xh, a.xl}, ff{b.xh, b.xl});
+  const ff dy = df_sub(ff{a.yh, a.yl}, ff{b.yh, b.yl});
+  const ff dz = df_sub(ff{a.zh, a.zl}, ff{b.zh, b.zl});
+  const ff r2 = df_norm2(dx, dy, dz);
+  const ff r = df_sqrt(r2);
+  const ff ex = df_exp(df_sub(rho, df_mul(rho, r)));
+  e = r2.hi > 0.f ? df_mul(ex, df_add_f(ex, -2.f)) : ff{__int_as_float(0x7f800000), 0.f};
+  const ff c = df_mul(df_mul(ex, df_add_f(ex, -1.f)), df_rcp(r));
+  vx = df_mul(c, dx); vy = df_mul(c, dy); vz = df_mul(c, dz);
+}
+
 // One row of the pair sum in df arithmetic, coordinates pre-scaled by
 // 1/sigma (so s2 = 1/r^2).  Accumulates acc_i = sum_j s2 s6 (2 s6 - 1) d_ij
 // and e_i = sum_j s6 (s6 - 1), both as df.

@@ -135,8 +135,8 @@ __device__ __forceinline__ int hidx(int slot, int a, int c, int rank) {
 // owns, the terms of all other atoms (deterministic, no shared pair buffer);
 // E = (eps / 2) sum_i sum_{j != i} e (e - 2), and
 // g_i = -(2 eps rho / re) sum_{j != i} e (e - 1) (x_i - x_j) / r.
-// FP32 (first tier of the mixed path; compensated energy) and FP64; the
-// mixed path has no double-float tier for this potential.  FP64 teams with
+// FP32 (first tier of the mixed path; compensated energy), double-float
+// (evaluate_morse_df, the polish tier) and FP64.  FP64 teams with
 // a half-pair buffer (clusters of up to 64 atoms) take each pair once, as
 // for Eq. (1): pair p's vector e (e - 1) (x_i - x_j) / r goes to the buffer,
 // then every (atom, component) row is summed, +v over j > i, -v over j < i.
@@ -154,6 +154,125 @@ __device__ __forceinline__ void pair_term_morse_f64(const PosD& a, const PosD& b
   vx = c * dx; vy = c * dy; vz = c * dz;
 }
 
+// Double-float Morse evaluation (the mixed path's polish tier): positions
+// scaled by 1/re, pair terms by pair_term_morse_df (double-float exponential
+// and square root); each pair once through the half-pair buffer for clusters
+// of up to 64 atoms, one-sided rows above.
+template <int T, int A, typename P>
+__device__ __forceinline__ void evaluate_morse_df(const Team<T>& tm, int n,
+                                                  const typename P::XP (&x)[A][3],
+                                                  typename P::XG (&g)[A][3], void* posv,
+                                                  void* hbuf, const MinParams& p,
+                                                  const typename P::V (*d)[3],
+                                                  typename P::F& E, typename P::S& dphi) {
+  using V = typename P::V;
+  using S = typename P::S;
+  PosDF* pos = static_cast<PosDF*>(posv);
+  tm.sync();  // previous readers of pos are done
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int i = tm.rank + a * T;
+    if (i < n) {
+      ff qx = x[a][0], qy = x[a][1], qz = x[a][2];
+      if (p.k.sigma != 1.0) {
+        const ff is{p.k.is_hi, p.k.is_lo};
+        qx = df_mul(qx, is); qy = df_mul(qy, is); qz = df_mul(qz, is);
+      }
+      pos[i] = PosDF{qx.hi, qy.hi, qz.hi, 0.f, qx.lo, qy.lo, qz.lo, 0.f};
+    }
+  }
+  tm.sync();
+  const ff rho{p.k.rho_f, p.k.rho_lo};
+  const float gs = p.k.m_g_f;
+  V dp = (V)0;
+  ff e{0.f, 0.f};
+  if (hbuf != nullptr && !p.tiled) {
+    const int np = n_pairs(n);
+    ff* vb = static_cast<ff*>(hbuf);
+    float* gsum = static_cast<float*>(posv);
+    int i1, j1, i2, j2;
+    pair_start(n, tm.rank, i1, j1);
+    i2 = i1; j2 = j1;
+    pair_advance(n, T, i2, j2);
+    for (int q = tm.rank; q < np; q += 2 * T) {
+      const bool two = q + T < np;
+      const int ib = two ? i2 : 0, jb = two ? j2 : 1;
+      ff ax, ay, az, ae, bx, by, bz, be;
+      pair_term_morse_df(pos[i1], pos[j1], rho, ax, ay, az, ae);
+      pair_term_morse_df(pos[ib], pos[jb], rho, bx, by, bz, be);
+      vb[q] = ax; vb[np + q] = ay; vb[2 * np + q] = az;
+      df_acc(e, ae);
+      if (two) {
+        vb[q + T] = bx; vb[np + q + T] = by; vb[2 * np + q + T] = bz;
+        df_acc(e, be);
+      }
+      pair_advance(n, 2 * T, i1, j1);
+      pair_advance(n, 2 * T, i2, j2);
+    }
+    tm.sync();
+    for (int q3 = tm.rank; q3 < 3 * n; q3 += T) {
+      const int ii = q3 / 3;
+      const ff* vc = vb + (q3 - 3 * ii) * np;
+      const int ri = row_base(n, ii);       // all lanes walk j together
+      int rj = -1;
+      ff sacc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      for (int j0 = 0; j0 < n; j0 += 4) {
+        ff v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          const int qq = j < ii ? rj + ii : ri + j;
+          v[u] = ff{0.f, 0.f};
+          if (j < n && j != ii) v[u] = vc[qq];
+          if (j < ii) v[u] = ff{-v[u].hi, -v[u].lo};
+          rj += n - j - 2;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) df_acc(sacc[u], v[u]);
+      }
+      const ff sum = df_add(df_add(sacc[0], sacc[1]), df_add(sacc[2], sacc[3]));
+      gsum[q3] = -gs * (sum.hi + sum.lo);
+    }
+    tm.sync();
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int ii = tm.rank + a * T;
+      if (ii < n) {
+        g[a][0] = gsum[3 * ii]; g[a][1] = gsum[3 * ii + 1]; g[a][2] = gsum[3 * ii + 2];
+      } else {
+        g[a][0] = 0.f; g[a][1] = 0.f; g[a][2] = 0.f;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    E = ff_scale(team_sum_ff<T>(tm, e), p.k.eps_f);
+  } else {
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int i = tm.rank + a * T;
+      if (i < n) {
+        const PosDF pi = pos[i];
+        ff ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
+        for (int j = 0; j < n; ++j) {
+          ff vx, vy, vz, ep;
+          pair_term_morse_df(pi, pos[j], rho, vx, vy, vz, ep);
+          if (j != i) {
+            df_acc(ax, vx); df_acc(ay, vy); df_acc(az, vz);
+            df_acc(e, ep);
+          }
+        }
+        g[a][0] = -gs * (ax.hi + ax.lo);
+        g[a][1] = -gs * (ay.hi + ay.lo);
+        g[a][2] = -gs * (az.hi + az.lo);
+      } else {
+        g[a][0] = 0.f; g[a][1] = 0.f; g[a][2] = 0.f;
+      }
+      if (d) dp += (V)g[a][0] * d[a][0] + (V)g[a][1] * d[a][1] + (V)g[a][2] * d[a][2];
+    }
+    E = ff_scale(team_sum_ff<T>(tm, e), p.k.m_half_f);
+  }
+  if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+}
+
 template <int T, int A, typename P>
 __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
                                                const typename P::XP (&x)[A][3],
@@ -164,7 +283,10 @@ __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
   using X = typename P::XP;
   using V = typename P::V;
   using S = typename P::S;
-  static_assert(P::PM == 0, "Morse pair terms are evaluated in FP32 or FP64 only");
+  if constexpr (P::PM == 1) {
+    evaluate_morse_df<T, A, P>(tm, n, x, g, posv, hbuf, p, d, E, dphi);
+    return;
+  } else {
   using Q = typename PosOf<X>::type;
   Q* pos = static_cast<Q*>(posv);
   tm.sync();  // previous readers of pos are done
@@ -336,6 +458,7 @@ __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
     E = team_sum_dd<T>(tm, e) * p.k.m_half;
   }
   if (d) dphi = (S)team_sum1<T, V>(tm, dp);
+  }
 }
 
 template <int T, int A, typename P>
@@ -1415,15 +1538,6 @@ __device__ __forceinline__ void minimise(const Team<T>& tm, int n, double (&x64)
 #pragma unroll
           for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
       }
-    } else if constexpr (POT != LJ_POT_LJ) {
-      // no double-float tier for this potential: FP32 hands over to FP64
-      if (moved32) {
-#pragma unroll
-        for (int a = 0; a < A; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) x64[a][c] = (double)x32[a][c];
-      }
-      need_fp64 = true;
     } else {
       // ---- tier 2: double-float positions and pair terms, FP32 elsewhere -----
       ff xdf[A][3];

@@ -18,12 +18,18 @@ import numpy as np
 SAME_BASIN_TOL = 1e-3
 
 
+RECORDS = []     # every record() of this session, printed in the terminal summary
+
+
 def record(tag, **metrics):
     """Print the achieved parity figures of a test and, when the environment
     variable LJ_PARITY_REPORT names a file, append them to it as one JSON
-    line, so that a run keeps the numbers its assertions were checked on."""
+    line, so that a run keeps the numbers its assertions were checked on.
+    The session's figures are also printed at its end (tests/conftest.py),
+    where a quiet run keeps them."""
     clean = {k: (float(v) if isinstance(v, (np.floating, np.integer)) else v)
              for k, v in metrics.items()}
+    RECORDS.append({"test": tag, **clean})
     print(f"[parity] {tag}: " + ", ".join(f"{k}={v}" for k, v in clean.items()))
     path = os.environ.get("LJ_PARITY_REPORT")
     if path:

@@ -151,6 +151,7 @@ def test_morse_invalid_arguments(lj, ctx):
     x = _cuda(np.zeros(6))
     e = torch.empty(1, dtype=torch.float64, device="cuda")
     for pot, rho in ((lj.LJ_POT_MORSE, 0.0), (lj.LJ_POT_MORSE, -1.0), (lj.LJ_POT_MORSE, math.inf),
+                     (lj.LJ_POT_MORSE, 65.0),
                      (7, 6.0)):
         with pytest.raises(lj.LjError) as ei:
             lj.lj_energy_grad_batched(ctx, x, e, n_cand=1, uniform_n=2, potential=pot, rho=rho)
@@ -266,3 +267,37 @@ def test_morse_bh_matches_oracle(lj, ctx, prec, n, K, steps, floor):
     record(f"morse_bh_n{n}_k{K}_p{prec}", steps_matching=strict, steps=total, fraction=frac,
            floor=floor)
     assert frac >= floor
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_morse_minimise_uneven_batch(lj, ctx, prec):
+    """An uneven Morse batch across the size buckets (one-sided rows, half-pair
+    FP64 up to 64 atoms, the 257..300-atom teams above): every GPU minimum is a
+    Morse minimum (FP64 gradient below gtol where converged, its energy), and
+    candidates both sides minimise into the same basin agree in energy."""
+    sizes = [5, 13, 31, 33, 38, 64, 65, 100, 150, 257, 300]
+    x0, off = I.uneven_cube_starts(sizes, 0.3, 2400 + prec)
+    n_cand = off.size - 1
+    xd = _cuda(x0)
+    e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+    st = torch.empty(n_cand, dtype=torch.int32, device="cuda")
+    lj.lbfgs_minimize_batched(ctx, xd, e, st, n_cand=n_cand, atom_offset=_cuda(off, torch.int64),
+                              max_n=max(sizes),
+                              params=lj.LbfgsParams(prec=prec, potential=lj.LJ_POT_MORSE, rho=RHO))
+    torch.cuda.synchronize()
+    xg, eg, sg = xd.cpu().numpy(), e.cpu().numpy(), st.cpu().numpy()
+    xo, eo, so, _, _ = O.lbfgs_batch(x0, n_cand, atom_off=off, potential=O.OBJ_MORSE, rho=RHO)
+    same = 0
+    for c in range(n_cand):
+        a0, a1 = 3 * off[c], 3 * off[c + 1]
+        e_chk, g_chk = O.morse_energy_grad(xg[a0:a1], 1.0, 1.0, RHO)
+        assert abs(e_chk - eg[c]) <= 1e-9 * max(1.0, abs(eg[c])), c
+        if sg[c] == O.CONVERGED:
+            assert np.abs(g_chk).max() < GTOL * 1.01, c
+        if sg[c] == O.CONVERGED and so[c] == O.CONVERGED and same_basin(xg[a0:a1], xo[a0:a1]):
+            same += 1
+            tol = FP64_REL * abs(eo[c]) if prec == 0 else MIX_ABS_FINAL
+            assert abs(eg[c] - eo[c]) <= tol, (c, eg[c], eo[c])
+    record(f"morse_minimise_uneven_p{prec}", same_basin=same, candidates=n_cand,
+           gpu_converged=int((sg == O.CONVERGED).sum()))
+    assert (sg == O.CONVERGED).mean() >= 0.9

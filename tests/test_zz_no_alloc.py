@@ -137,3 +137,43 @@ def test_noalloc_large_clusters_with_capped_grid(lj):
         assert stats["minimisations"] == n_cand
         assert np.array_equal(sg, sr)
         assert np.all(np.abs(eg - er) <= FP64_REL_E * np.abs(er))
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_noalloc_morse_matches_context_entry_point(lj, prec):
+    """The no-allocation entry point takes the pair potential from the same
+    parameters (Morse, rho = 6, an uneven batch across buckets): results equal
+    the context entry point's."""
+    sizes = I.uneven_sizes(24, 8, 80, I.workload_seed(3) + 70)
+    x0, off = I.uneven_cube_starts(sizes, 0.3, I.workload_seed(3) + 71)
+    n_cand = off.size - 1
+    p = lj.LbfgsParams(prec=prec, potential=lj.LJ_POT_MORSE, rho=6.0)
+    offd = torch.as_tensor(off, device="cuda")
+
+    def run(noalloc):
+        x = torch.as_tensor(x0, dtype=torch.float64, device="cuda").contiguous()
+        e = torch.empty(n_cand, dtype=torch.float64, device="cuda")
+        st = torch.empty(n_cand, dtype=torch.int32, device="cuda")
+        if noalloc:
+            lib = lj.load()
+            b = lj._Batch(n_cand, 0, offd.data_ptr(), int(np.diff(off).max()))
+            pc = p.c()
+            rc = lib.lbfgs_minimize_batched_noalloc(C.byref(b), C.byref(pc), x.data_ptr(),
+                                                    e.data_ptr(), st.data_ptr(), None, None, None,
+                                                    torch.cuda.current_stream().cuda_stream)
+            assert rc == lj.LJ_OK
+        else:
+            ctx = lj.Ctx(0)
+            lj.lbfgs_minimize_batched(ctx, x, e, st, n_cand=n_cand, atom_offset=offd,
+                                      max_n=int(np.diff(off).max()), params=p)
+            torch.cuda.synchronize()
+            ctx.close()
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), e.cpu().numpy(), st.cpu().numpy()
+
+    xr, er, sr = run(False)
+    xg, eg, sg = run(True)
+    assert np.array_equal(sg, sr)
+    fin = np.isfinite(er)
+    tol = FP64_REL_E * np.abs(er[fin]) if prec == 0 else MIX_ABS_FINAL
+    assert np.all(np.abs(eg[fin] - er[fin]) <= tol)
