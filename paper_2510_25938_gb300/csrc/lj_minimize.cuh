@@ -827,7 +827,7 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 }
 
 // ---------------------------------------------------------------------------
-// Two-loop recursion by the team's first warp (float history, teams of 2 to 4
+// Two-loop recursion by the team's first warp (float history, teams of 1 to 4
 // warps).  The recursion is a chain of 2 cnt + 1 dependent inner products;
 // done by the whole team, each one crosses warps through shared memory and a
 // barrier.  Instead every thread stages its gradient in `xb` (the idle
@@ -1102,7 +1102,7 @@ __device__ __forceinline__ int run_phase(const Team<T>& tm, int n, typename P::X
     long long tc = clock64();
     S dphi0 = (S)1;
     bool led = false;
-    if constexpr (std::is_same<V, float>::value && T > 32 && T <= 128) {
+    if constexpr (std::is_same<V, float>::value && T <= 128) {
       if (cnt > 0 && 12 * A * T + 4 <= 32 * n) {
         dphi0 = (S)lead_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh, rho, gmv, sup, g,
                                            static_cast<float*>(pos), d);
