@@ -827,8 +827,9 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 }
 
 // ---------------------------------------------------------------------------
-// Two-loop recursion by the team's first warp (float history, teams of 1 to 4
-// warps).  The recursion is a chain of 2 cnt + 1 dependent inner products;
+// Two-loop recursion by the team's first warp (teams of 1 to 4 warps; float
+// history staged through the idle position buffer, FP64 history through the
+// idle half-pair buffer).  The recursion is a chain of 2 cnt + 1 dependent inner products;
 // done by the whole team, each one crosses warps through shared memory and a
 // barrier.  Instead every thread stages its gradient in `xb` (the idle
 // position buffer, 12 A T + 4 bytes), warp 0 runs the recursion over all T
@@ -847,13 +848,15 @@ __device__ __forceinline__ S cubic_step(S a, F fa, S ga, S b, F fb, S gb) {
 // recursion (Algorithm 7.4 of Nocedal & Wright), half as many dependent
 // reductions.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v) {   // xor butterfly: every lane gets the sum
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {   // xor butterfly: every lane gets the sum
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
 
-__device__ __forceinline__ void warp_sum2(float& v0, float& v1) {
+template <typename V>
+__device__ __forceinline__ void warp_sum2(V& v0, V& v1) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v0 += __shfl_xor_sync(kFull, v0, o);
@@ -861,26 +864,23 @@ __device__ __forceinline__ void warp_sum2(float& v0, float& v1) {
   }
 }
 
-template <int T, int A, typename XG>
-__device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt, int head,
-                                               const float* __restrict__ Sh,
-                                               const float* __restrict__ Yh,
-                                               const float (&rho)[LJ_MAX_M],
-                                               const float (&gmv)[LJ_MAX_M],
-                                               const float (&sup)[LJ_MAX_M],
-                                               const XG (&g)[A][3], float* xb,
-                                               float (&d)[A][3]) {
+template <int T, int A, typename XG, typename V>
+__device__ __forceinline__ V lead_two_loop(const Team<T>& tm, int m, int cnt, int head,
+                                           const V* __restrict__ Sh, const V* __restrict__ Yh,
+                                           const V (&rho)[LJ_MAX_M], const V (&gmv)[LJ_MAX_M],
+                                           const V (&sup)[LJ_MAX_M], const XG (&g)[A][3],
+                                           V* xb, V (&d)[A][3]) {
   constexpr int W = T / 32;
 #pragma unroll
   for (int a = 0; a < A; ++a)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) xb[(a * 3 + c) * T + tm.rank] = (float)g[a][c];
+    for (int c = 0; c < 3; ++c) xb[(a * 3 + c) * T + tm.rank] = (V)g[a][c];
   tm.sync();
   if (tm.rank < 32) {
     const int lane = tm.rank;
     auto slot_of = [&](int t) { const int sl = head + t; return sl >= m ? sl - m : sl; };
-    float q[W][A][3], gl[W][A][3];
-    float alpha[LJ_MAX_M];
+    V q[W][A][3], gl[W][A][3];
+    V alpha[LJ_MAX_M];
 #pragma unroll
     for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -894,7 +894,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
     int t = cnt - 1;
     for (; t >= 1; t -= 2) {
       const int s0 = slot_of(t), s1 = slot_of(t - 1);
-      float sv0[W][A][3], yv0[W][A][3], sv1[W][A][3], yv1[W][A][3];
+      V sv0[W][A][3], yv0[W][A][3], sv1[W][A][3], yv1[W][A][3];
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -906,8 +906,8 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
             sv1[w][a][c] = Sh[hidx<T, A>(s1, a, c, lane + 32 * w)];
             yv1[w][a][c] = Yh[hidx<T, A>(s1, a, c, lane + 32 * w)];
           }
-      const float r0 = rho[s0], r1 = rho[s1], u01 = sup[s0];
-      float p0 = 0.f, p1 = 0.f;
+      const V r0 = rho[s0], r1 = rho[s1], u01 = sup[s0];
+      V p0 = (V)0, p1 = (V)0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -918,8 +918,8 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
             p1 += sv1[w][a][c] * q[w][a][c];
           }
       warp_sum2(p0, p1);
-      const float a0 = r0 * p0;
-      const float a1 = r1 * (p1 - a0 * u01);
+      const V a0 = r0 * p0;
+      const V a1 = r1 * (p1 - a0 * u01);
       alpha[t] = a0;
       alpha[t - 1] = a1;
 #pragma unroll
@@ -934,7 +934,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
     }
     if (t == 0) {
       const int s0 = slot_of(0);
-      float sv0[W][A][3], yv0[W][A][3];
+      V sv0[W][A][3], yv0[W][A][3];
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -944,14 +944,14 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
             sv0[w][a][c] = Sh[hidx<T, A>(s0, a, c, lane + 32 * w)];
             yv0[w][a][c] = Yh[hidx<T, A>(s0, a, c, lane + 32 * w)];
           }
-      float part = 0.f;
+      V part = (V)0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
           for (int c = 0; c < 3; ++c) part += sv0[w][a][c] * q[w][a][c];
-      const float a0 = rho[s0] * warp_sum(part);
+      const V a0 = rho[s0] * warp_sum(part);
       alpha[0] = a0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
@@ -960,7 +960,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 #pragma unroll
           for (int c = 0; c < 3; ++c) q[w][a][c] -= a0 * yv0[w][a][c];
     }
-    const float gam = gmv[slot_of(cnt - 1)];
+    const V gam = gmv[slot_of(cnt - 1)];
 #pragma unroll
     for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -971,7 +971,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
     t = 0;
     for (; t + 1 < cnt; t += 2) {
       const int s0 = slot_of(t), s1 = slot_of(t + 1);
-      float sv0[W][A][3], yv0[W][A][3], sv1[W][A][3], yv1[W][A][3];
+      V sv0[W][A][3], yv0[W][A][3], sv1[W][A][3], yv1[W][A][3];
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -983,9 +983,9 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
             sv1[w][a][c] = Sh[hidx<T, A>(s1, a, c, lane + 32 * w)];
             yv1[w][a][c] = Yh[hidx<T, A>(s1, a, c, lane + 32 * w)];
           }
-      const float r0 = rho[s0], r1 = rho[s1], u01 = sup[s1];
-      const float al0 = alpha[t], al1 = alpha[t + 1];
-      float p0 = 0.f, p1 = 0.f;
+      const V r0 = rho[s0], r1 = rho[s1], u01 = sup[s1];
+      const V al0 = alpha[t], al1 = alpha[t + 1];
+      V p0 = (V)0, p1 = (V)0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -996,8 +996,8 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
             p1 += yv1[w][a][c] * q[w][a][c];
           }
       warp_sum2(p0, p1);
-      const float c0 = al0 - r0 * p0;
-      const float c1 = al1 - r1 * (p1 + c0 * u01);
+      const V c0 = al0 - r0 * p0;
+      const V c1 = al1 - r1 * (p1 + c0 * u01);
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -1010,7 +1010,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
     }
     if (t < cnt) {
       const int s0 = slot_of(t);
-      float sv0[W][A][3], yv0[W][A][3];
+      V sv0[W][A][3], yv0[W][A][3];
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -1020,14 +1020,14 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
             sv0[w][a][c] = Sh[hidx<T, A>(s0, a, c, lane + 32 * w)];
             yv0[w][a][c] = Yh[hidx<T, A>(s0, a, c, lane + 32 * w)];
           }
-      float part = 0.f;
+      V part = (V)0;
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
           for (int c = 0; c < 3; ++c) part += yv0[w][a][c] * q[w][a][c];
-      const float c0 = alpha[t] - rho[s0] * warp_sum(part);
+      const V c0 = alpha[t] - rho[s0] * warp_sum(part);
 #pragma unroll
       for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -1035,7 +1035,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
 #pragma unroll
           for (int c = 0; c < 3; ++c) q[w][a][c] += c0 * sv0[w][a][c];
     }
-    float part = 0.f;
+    V part = (V)0;
 #pragma unroll
     for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -1045,7 +1045,7 @@ __device__ __forceinline__ float lead_two_loop(const Team<T>& tm, int m, int cnt
           xb[(a * 3 + c) * T + lane + 32 * w] = -q[w][a][c];
           part += gl[w][a][c] * -q[w][a][c];
         }
-    const float dphi = warp_sum(part);
+    const V dphi = warp_sum(part);
     if (lane == 0) xb[A * 3 * T] = dphi;
   }
   tm.sync();
@@ -1102,10 +1102,19 @@ __device__ __forceinline__ int run_phase(const Team<T>& tm, int n, typename P::X
     long long tc = clock64();
     S dphi0 = (S)1;
     bool led = false;
-    if constexpr (std::is_same<V, float>::value && T <= 128) {
-      if (cnt > 0 && 12 * A * T + 4 <= 32 * n) {
-        dphi0 = (S)lead_two_loop<T, A, XG>(tm, m, cnt, head, Sh, Yh, rho, gmv, sup, g,
-                                           static_cast<float*>(pos), d);
+    if constexpr (T <= 128) {
+      // staging buffer for the lead warp: the idle position buffer (32 n
+      // bytes) for float history, the idle half-pair buffer (24 bytes per
+      // pair) for double history
+      V* xb = nullptr;
+      if constexpr (std::is_same<V, float>::value) {
+        if (12 * A * T + 4 <= 32 * n) xb = static_cast<V*>(pos);
+      } else {
+        if (hbuf != nullptr && !p.tiled && 24 * A * T + 8 <= 24 * n_pairs(n))
+          xb = static_cast<V*>(hbuf);
+      }
+      if (cnt > 0 && xb != nullptr) {
+        dphi0 = (S)lead_two_loop<T, A, XG, V>(tm, m, cnt, head, Sh, Yh, rho, gmv, sup, g, xb, d);
         vec += (long long)cnt * 3 * n;
         led = true;
       }
