@@ -596,10 +596,14 @@ def sequential_lj13_record(L, reps, warmup):
             torch.cuda.synchronize()
             if rep >= max(warmup, 1):
                 times.append(ev0.elapsed_time(ev1) / 1e3)
-                conv = L.stats_dict(stats)["converged"]
+                sd = L.stats_dict(stats)
+                conv = sd["converged"]
         t = sum(times) / len(times)
         out[pname] = {"bh_steps_per_s": n_steps / t, "ms_per_200_steps": 1e3 * t,
-                      "value": conv / t, "unit": "converged minimisations/s"}
+                      "value": conv / t, "unit": "converged minimisations/s",
+                      "per_minimisation": {k: sd[k] / max(sd["minimisations"], 1) for k in (
+                          "evals32", "evals_df", "evals64", "iters32", "iters64", "cycles32",
+                          "cycles_df", "cycles64", "cycles_direction", "cycles_linesearch")}}
     ctx.close()
     ost = bh_state_np(xm.reshape(1, -1), em, 0.4)
     t0 = time.perf_counter()
