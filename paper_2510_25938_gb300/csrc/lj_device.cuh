@@ -395,6 +395,59 @@ __device__ __forceinline__ void pair_row_f32x2(int n, int i, float px, float py,
   bz = __fadd_rn(az.x, az.y);
 }
 
+// One-sided Morse row of atom i on the same packed records (unscaled
+// coordinates): with r from r^2 and a reciprocal square root, e = exp(rho -
+// rr r) (rr = rho / re; FP32 __expf), b = sum_j e (e - 1) (x_j - x_i) / r and
+// e_row += sum_j e (e - 2), the self term excluded; the padding atom's terms
+// vanish (its exponential underflows to 0).  Energy blocks as in
+// pair_row_f32x2 (float-float).
+__device__ __forceinline__ void morse_row_f32x2(int n, int i, float px, float py, float pz,
+                                                const PosF2* __restrict__ pos, float rho,
+                                                float rr, float& bx, float& by, float& bz,
+                                                ff& e) {
+  const int M = (n + 1) >> 1;
+  const float2 npx = f2(-px), npy = f2(-py), npz = f2(-pz);
+  const float2 nrr = f2(-rr), rho2 = f2(rho), m1 = f2(-1.f), m2 = f2(-2.f);
+  const int sx = (i & 1) ? -1 : (i >> 1);     // record whose lane 0 is atom i
+  const int sy = (i & 1) ? (i >> 1) : -1;     // record whose lane 1 is atom i
+  float2 ax = f2(0.f), ay = f2(0.f), az = f2(0.f);
+  auto term = [&](int m, float2& eb) {
+    const float4 xy = *reinterpret_cast<const float4*>(&pos[m].x[0]);
+    const float2 zz = *reinterpret_cast<const float2*>(&pos[m].z[0]);
+    const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
+    const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
+    const float2 dz = __fadd2_rn(zz, npz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float2 ir = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (m == sx) ir.x = 0.f;                   // the self term: r = 0 instead of 0 * inf
+    if (m == sy) ir.y = 0.f;
+    const float2 x = __ffma2_rn(nrr, __fmul2_rn(r2, ir), rho2);      // rho (1 - r / re)
+    float2 ex = make_float2(__expf(x.x), __expf(x.y));
+    if (m == sx) ex.x = 0.f;
+    if (m == sy) ex.y = 0.f;
+    eb = __ffma2_rn(ex, __fadd2_rn(ex, m2), eb);
+    const float2 c = __fmul2_rn(__fmul2_rn(ex, __fadd2_rn(ex, m1)), ir);
+    ax = __ffma2_rn(c, dx, ax);
+    ay = __ffma2_rn(c, dy, ay);
+    az = __ffma2_rn(c, dz, az);
+  };
+  int m = 0;
+  for (; m + 4 <= M; m += 4) {
+    float2 eb = f2(0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) term(m + u, eb);
+    e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
+  }
+  if (m < M) {
+    float2 eb = f2(0.f);
+    for (; m < M; ++m) term(m, eb);
+    e = ff_add_f(e, __fadd_rn(eb.x, eb.y));
+  }
+  bx = __fadd_rn(ax.x, ax.y);
+  by = __fadd_rn(ay.x, ay.y);
+  bz = __fadd_rn(az.x, az.y);
+}
+
 // Double-double helpers: exact sum a + b = s + e (Knuth TwoSum).
 struct dd {
   double hi, lo;

@@ -288,51 +288,36 @@ __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
     return;
   } else {
   using Q = typename PosOf<X>::type;
-  Q* pos = static_cast<Q*>(posv);
   tm.sync();  // previous readers of pos are done
 #pragma unroll
   for (int a = 0; a < A; ++a) {
     const int i = tm.rank + a * T;
     if (i < n) {
-      Q q;
-      q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
-      pos[i] = q;
+      if constexpr (sizeof(X) == 4) {
+        stage_f32x2(static_cast<PosF2*>(posv), n, i, x[a][0], x[a][1], x[a][2]);   // packed
+      } else {
+        Q q;
+        q.x = x[a][0]; q.y = x[a][1]; q.z = x[a][2]; q.w = (X)0;
+        static_cast<Q*>(posv)[i] = q;
+      }
     }
   }
   tm.sync();
   V dp = (V)0;
   if constexpr (sizeof(X) == 4) {
-    const float rho = p.k.rho_f, rr = p.k.rho_re_f, gsc = p.k.m_g_f;
-    const float kInfF = __int_as_float(0x7f800000);
+    // packed rows: two pair terms per instruction, as for Eq. (1)
+    const PosF2* pos = static_cast<const PosF2*>(posv);
+    const float gsc = p.k.m_g_f;
     ff e{0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       const int i = tm.rank + a * T;
       if (i < n) {
-        const float xi = x[a][0], yi = x[a][1], zi = x[a][2];
-        float ax = 0.f, ay = 0.f, az = 0.f;
+        float bx, by, bz;
         ff ea{0.f, 0.f};
-#pragma unroll 2
-        for (int j = 0; j < n; ++j) {
-          const Q q = pos[j];
-          const float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float ir = rsqrtf(r2);
-          const float ex = __expf(fmaf(-rr, r2 * ir, rho));   // e^{rho (1 - r/re)}
-          float term = ex * (ex - 2.f);
-          float c = ex * (ex - 1.f) * ir;
-          if (j == i) {
-            term = 0.f;
-            c = 0.f;
-          } else if (!(r2 > 0.f)) {
-            term = kInfF;
-          }
-          ea = ff_add_f(ea, term);
-          ax = fmaf(c, dx, ax);
-          ay = fmaf(c, dy, ay);
-          az = fmaf(c, dz, az);
-        }
-        g[a][0] = -gsc * ax; g[a][1] = -gsc * ay; g[a][2] = -gsc * az;
+        morse_row_f32x2(n, i, x[a][0], x[a][1], x[a][2], pos, p.k.rho_f, p.k.rho_re_f, bx, by,
+                        bz, ea);
+        g[a][0] = gsc * bx; g[a][1] = gsc * by; g[a][2] = gsc * bz;
         e = ff_add(e, ea);
       } else {
         g[a][0] = 0.f; g[a][1] = 0.f; g[a][2] = 0.f;
@@ -415,6 +400,7 @@ __device__ __forceinline__ void evaluate_morse(const Team<T>& tm, int n,
     }
     E = team_sum_dd<T>(tm, e) * p.k.eps;
   } else {
+    const Q* pos = static_cast<const Q*>(posv);
     const double rho = p.k.rho, rr = p.k.rho_re, gsc = p.k.m_g;
     const double kInf = __longlong_as_double(0x7ff0000000000000LL);
     dd e{0.0, 0.0};
