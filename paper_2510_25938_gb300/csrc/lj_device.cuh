@@ -145,8 +145,14 @@ __device__ __forceinline__ ff ff_add_f(ff a, float b) {
   ff s = ff_two_sum(a.hi, b);
   return ff_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
 }
-__device__ __forceinline__ ff ff_scale(ff a, float c) {   // c exact power of two or
-  return ff{a.hi * c, a.lo * c};                          // small integer: near-exact
+// a c for a float-float a and an FP32 constant c: the high product exact by
+// TwoProd (FMA), the low word's product and that error added, renormalised;
+// ~2^-47 relative for any c (for a power of two it is the exact product)
+__device__ __forceinline__ ff ff_scale(ff a, float c) {
+  const float p = __fmul_rn(a.hi, c);
+  const float lo = fmaf(a.lo, c, fmaf(a.hi, c, -p));
+  const float s = __fadd_rn(p, lo);
+  return ff{s, __fsub_rn(lo, __fsub_rn(s, p))};
 }
 
 // energy-value traits: difference, finiteness, conversion

@@ -301,3 +301,42 @@ def test_morse_minimise_uneven_batch(lj, ctx, prec):
     record(f"morse_minimise_uneven_p{prec}", same_basin=same, candidates=n_cand,
            gpu_converged=int((sg == O.CONVERGED).sum()))
     assert (sg == O.CONVERGED).mean() >= 0.9
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_morse_minimise_eps_re(lj, ctx, prec):
+    """Morse with eps = 0.7, re = 1.3, rho = 10: every GPU minimum is a
+    minimum of that potential, same-basin energies agree with the oracle's,
+    and the mixed path's polish stays in double-float (about one FP64
+    evaluation per minimisation)."""
+    n, nc, rho = 13, 24, 10.0
+    x0 = I.cube_starts(nc, n, 2.0 * 1.3, 2500)
+    xo, eo, so, _, _ = O.lbfgs_batch(x0, nc, uniform_n=n, eps=0.7, sigma=1.3,
+                                     potential=O.OBJ_MORSE, rho=rho)
+    xo = xo.reshape(nc, -1)
+    xd = _cuda(x0.reshape(-1))
+    e = torch.empty(nc, dtype=torch.float64, device="cuda")
+    st = torch.empty(nc, dtype=torch.int32, device="cuda")
+    stats = lj.new_stats()
+    lj.lbfgs_minimize_batched(ctx, xd, e, st, None, None, stats, n_cand=nc, uniform_n=n,
+                              params=lj.LbfgsParams(prec=prec, eps=0.7, sigma=1.3,
+                                                    potential=lj.LJ_POT_MORSE, rho=rho))
+    torch.cuda.synchronize()
+    xg, eg, sg = xd.cpu().numpy().reshape(nc, -1), e.cpu().numpy(), st.cpu().numpy()
+    same = 0
+    for c in range(nc):
+        e_chk, g_chk = O.morse_energy_grad(xg[c], 0.7, 1.3, rho)
+        assert abs(e_chk - eg[c]) <= 1e-9 * max(1.0, abs(eg[c])), c
+        if sg[c] == O.CONVERGED:
+            assert np.abs(g_chk).max() < GTOL * 1.01, c
+        if sg[c] == O.CONVERGED and so[c] == O.CONVERGED and same_basin(xg[c], xo[c]):
+            same += 1
+            tol = FP64_REL * abs(eo[c]) if prec == 0 else MIX_ABS_FINAL
+            assert abs(eg[c] - eo[c]) <= tol, (c, eg[c], eo[c])
+    sd = lj.stats_dict(stats)
+    record(f"morse_minimise_eps_re_p{prec}", same_basin=same, candidates=nc,
+           gpu_converged=int((sg == O.CONVERGED).sum()),
+           fp64_evals_per_minimisation=sd["evals64"] / nc)
+    assert (sg == O.CONVERGED).mean() >= 0.95
+    if prec == 2:
+        assert sd["evals64"] / nc < 3.0     # the FP64 path: ~100 per minimisation

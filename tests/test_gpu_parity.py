@@ -878,3 +878,43 @@ def test_uneven_4096_full_size_sampled(lj, ctx):
     _compare_minima(x_sub, sub_off, xg_sub, eg[sample], sg[sample], xo, eo, so,
                     MIX_ABS_FINAL, 0.0, 0.0, "uneven_4096_sampled_mixed")
     record("uneven_4096_full_size", converged_fraction=float((sg == O.CONVERGED).mean()))
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_minimise_eps_sigma(lj, ctx, prec):
+    """Eq. (1) with eps = 0.7, sigma = 1.3 (neither a power of two): the
+    minimiser's tiers scale energies and gradients by the host-derived
+    constants, and the double-float tier stages positions scaled by 1/sigma.
+    Every GPU minimum is a minimum of that potential, and minima both sides
+    reach in the same basin agree in energy; the mixed path needs no more
+    FP64 evaluations than with eps = sigma = 1 (its polish stays in
+    double-float)."""
+    n, nc = 13, 24
+    x0 = I.cube_starts(nc, n, 2.0 * 1.3, I.workload_seed(0) + 500)
+    xo, eo, so, _, _ = O.lbfgs_batch(x0, nc, uniform_n=n, eps=0.7, sigma=1.3)
+    xo = xo.reshape(nc, -1)
+    xd = _cuda(x0.reshape(-1))
+    e = torch.empty(nc, dtype=torch.float64, device="cuda")
+    st = torch.empty(nc, dtype=torch.int32, device="cuda")
+    stats = lj.new_stats()
+    lj.lbfgs_minimize_batched(ctx, xd, e, st, None, None, stats, n_cand=nc, uniform_n=n,
+                              params=lj.LbfgsParams(prec=prec, eps=0.7, sigma=1.3))
+    torch.cuda.synchronize()
+    xg, eg, sg = xd.cpu().numpy().reshape(nc, -1), e.cpu().numpy(), st.cpu().numpy()
+    same = 0
+    for c in range(nc):
+        e_chk, g_chk = O.lj_energy_grad(xg[c], 0.7, 1.3)
+        assert abs(e_chk - eg[c]) <= 1e-9 * abs(eg[c]), c
+        if sg[c] == O.CONVERGED:
+            assert np.abs(g_chk).max() < GTOL * 1.01, c
+        if sg[c] == O.CONVERGED and so[c] == O.CONVERGED and same_basin(xg[c], xo[c]):
+            same += 1
+            tol = FP64_REL_E * abs(eo[c]) if prec == 0 else MIX_ABS_FINAL
+            assert abs(eg[c] - eo[c]) <= tol, (c, eg[c], eo[c])
+    sd = lj.stats_dict(stats)
+    record(f"minimise_eps_sigma_p{prec}", same_basin=same, candidates=nc,
+           gpu_converged=int((sg == O.CONVERGED).sum()),
+           fp64_evals_per_minimisation=sd["evals64"] / nc)
+    assert (sg == O.CONVERGED).mean() >= 0.95
+    if prec == 2:
+        assert sd["evals64"] / nc < 3.0     # the FP64 path: ~100 per minimisation
