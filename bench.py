@@ -72,7 +72,7 @@ FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of G
 # dram__bytes_read.sum + dram__bytes_write.sum of one bh_cluster_kernel launch of this
 # workload (10 BH steps), from one ncu capture of the kernel as it is built now; None
 # whenever the kernel changes until it is captured again
-BH_DRAM_BYTES_PER_LAUNCH = 367616
+BH_DRAM_BYTES_PER_LAUNCH = 364288
 
 
 def parse():

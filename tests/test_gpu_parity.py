@@ -918,3 +918,54 @@ def test_minimise_eps_sigma(lj, ctx, prec):
     assert (sg == O.CONVERGED).mean() >= 0.95
     if prec == 2:
         assert sd["evals64"] / nc < 3.0     # the FP64 path: ~100 per minimisation
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_bh_shards_reproduce_unsharded_run(lj, ctx, prec):
+    """Walkers are independent and every random number is keyed by the
+    global walker index (walker0 + local index): 8 walkers in one launch and
+    the same walkers as two shards (walker0 = 0 and 3) in separate launches
+    give bit-identical states and traces -- what a run split across GPUs
+    relies on."""
+    W, n, K, steps, seed = 8, 13, 4, 12, 4242
+    st = _bh_start(W, n, 2.0, seed)
+    p = dict(K=K, kT=0.8, seed=seed, n_steps=steps, min=lj.LbfgsParams(prec=prec))
+    full = _gpu_state(lj, st)
+    trf = lj.new_trace(steps, W, K)
+    lj.bh_step_batched(ctx, full, lj.BhParams(walker0=0, **p), trf)
+    torch.cuda.synchronize()
+    parts = []
+    for a, b in ((0, 3), (3, 8)):
+        sub = {k: v[a:b].copy() for k, v in st.items()}
+        gs = _gpu_state(lj, sub)
+        tr = lj.new_trace(steps, b - a, K)
+        lj.bh_step_batched(ctx, gs, lj.BhParams(walker0=a, **p), tr)
+        torch.cuda.synchronize()
+        parts.append((gs, tr))
+    for k in ("x_cur", "e_cur", "x_best", "e_best", "stepsize", "win_accept", "n_accept"):
+        joined = np.concatenate([g[k].cpu().numpy() for g, _ in parts])
+        assert np.array_equal(joined, full[k].cpu().numpy()), k
+    for k in ("trial_e", "accepted", "stepsize", "best_trial_e"):
+        joined = np.concatenate([t[k].cpu().numpy() for _, t in parts], axis=1)
+        assert np.array_equal(joined, trf[k].cpu().numpy()), k
+
+
+def test_bh_adaptation_drives_acceptance_toward_target(lj, ctx):
+    """Started with a step far too large (1.5 sigma: almost every trial move
+    is rejected), the adaptation shrinks the step window by window until the
+    acceptance rate sits around the 50% target (Methodology, step 5)."""
+    W, n, steps, seed = 16, 13, 300, 99
+    st = _bh_start(W, n, 2.0, seed, step0=1.5)
+    gs = _gpu_state(lj, st)
+    tr = lj.new_trace(steps, W, 1)
+    lj.bh_step_batched(ctx, gs, lj.BhParams(K=1, kT=0.8, seed=seed, n_steps=steps,
+                                            min=lj.LbfgsParams(prec=2)), tr)
+    torch.cuda.synchronize()
+    acc = tr["accepted"].cpu().numpy().astype(float)
+    step = tr["stepsize"].cpu().numpy()
+    first, last = acc[:20].mean(), acc[-100:].mean()
+    record("bh_adaptation", first_20_steps_acceptance=first, last_100_steps_acceptance=last,
+           step_start=float(step[0].mean()), step_end=float(step[-1].mean()))
+    assert step[-1].mean() < 0.6 * step[0].mean()
+    assert first < 0.35
+    assert 0.3 <= last <= 0.7
