@@ -22,6 +22,11 @@ struct lj_ctx {
   size_t aux_bytes = 0;
   bool reserved = false;
   unsigned long long* queue = nullptr; // persistent-kernel work counter
+  // size buckets of an uneven batch run side by side: one stream each, forked
+  // from and joined back into the caller's stream with events (capturable)
+  cudaStream_t bucket_stream[ljh::kMaxBuckets] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[ljh::kMaxBuckets] = {};
   int bh_team = 0;                     // LJ_OPT_BH_TEAM (0 = automatic)
   int lbfgs_team = 0;                  // LJ_OPT_LBFGS_TEAM (0 = automatic)
   int tune_team[ljh::kMaxBuckets] = {};  // lj_ctx_autotune: team per size bucket (0 = none)
@@ -263,6 +268,11 @@ lj_status lj_ctx_create(lj_ctx** out, int device) {
   if (!g.ok) { delete c; return LJ_ERR_CUDA; }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (cudaMalloc(&c->queue, 64) != cudaSuccess) { delete c; return LJ_ERR_CUDA; }
+  bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int b = 0; b < ljh::kMaxBuckets && ok; ++b)
+    ok = cudaStreamCreateWithFlags(&c->bucket_stream[b], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->join_ev[b], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) { lj_ctx_destroy(c); return LJ_ERR_CUDA; }
   *out = c;
   return LJ_OK;
 }
@@ -275,6 +285,11 @@ lj_status lj_ctx_destroy(lj_ctx* ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->queue) cudaFree(ctx->queue);
+    for (int b = 0; b < ljh::kMaxBuckets; ++b) {
+      if (ctx->bucket_stream[b]) cudaStreamDestroy(ctx->bucket_stream[b]);
+      if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   }
   delete ctx;
   return LJ_OK;
@@ -414,13 +429,22 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
     ljh::Buckets bk;
     for (int b = 0; b < ljh::kMaxBuckets; ++b) bk.bound[b] = b < nb - 1 ? kBound[b] : max_n;
     ljh::Plan plans[ljh::kMaxBuckets];
-    size_t hist_need = 0;
+    size_t hist_need = 0, hist_sum = 0;
+    size_t hist_off[ljh::kMaxBuckets] = {};
     for (int b = 0; b < nb; ++b) {
       cudaError_t e = plan_for(bk.bound[b], &plans[b]);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched plan");
-      hist_need = std::max(hist_need, (size_t)plans[b].slots * plans[b].slot_bytes);
+      const size_t hb = ((size_t)plans[b].slots * plans[b].slot_bytes + 255) & ~size_t(255);
+      hist_off[b] = hist_sum;
+      hist_sum += hb;
+      hist_need = std::max(hist_need, hb);
     }
-    st = ensure_ws(ctx, hist_need);
+    // Buckets run side by side (their persistent launches share the GPU and
+    // overlap each other's tails) when every bucket can have its own history
+    // region: always without a reservation, within one otherwise; else one
+    // after another in the caller's stream, sharing one region.
+    const bool side_by_side = !ctx->reserved || hist_sum <= ctx->ws_bytes;
+    st = ensure_ws(ctx, side_by_side ? hist_sum : hist_need);
     if (st != LJ_OK) return st;
     st = ensure_aux(ctx, aux_bytes_for(batch->n_cand));
     if (st != LJ_OK) return st;
@@ -431,6 +455,10 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
     cudaError_t e = ljh::bucketize_launch(batch->d_atom_offset, batch->n_cand, nb, bk, counts,
                                           lists, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched bucketize");
+    if (side_by_side) {
+      e = cudaEventRecord(ctx->fork_ev, (cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched fork");
+    }
     for (int b = 0; b < nb; ++b) {
       ljh::LbfgsArgs a;
       a.n_cand = batch->n_cand;
@@ -446,12 +474,21 @@ lj_status lbfgs_minimize_batched(lj_ctx* ctx, const lj_batch* batch, const lj_lb
       a.nevals = d_nevals;
       a.stats = d_stats;
       a.queue = queues + b;
-      a.hist = ctx->ws;
+      a.hist = side_by_side ? static_cast<unsigned char*>(ctx->ws) + hist_off[b] : ctx->ws;
       a.hist_slot_bytes = plans[b].slot_bytes;
       a.hist_on_chip = plans[b].hist_on_chip;
       a.list = lists + (size_t)b * batch->n_cand;
       a.list_count = counts + b;
-      e = ljh::lbfgs_launch(a, plans[b], (cudaStream_t)stream);
+      if (!side_by_side) {
+        e = ljh::lbfgs_launch(a, plans[b], (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
+        continue;
+      }
+      cudaStream_t sb = ctx->bucket_stream[b];
+      e = cudaStreamWaitEvent(sb, ctx->fork_ev, 0);
+      if (e == cudaSuccess) e = ljh::lbfgs_launch(a, plans[b], sb);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->join_ev[b], sb);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, ctx->join_ev[b], 0);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "lbfgs_minimize_batched launch");
     }
     return LJ_OK;
