@@ -7,8 +7,8 @@ uniform in a cube of side 3.2 sigma (seeded), minimised once before timing;
 perturbations +-step per coordinate from Philox (initial step 0.4 sigma,
 adapted every 10 steps toward 50% acceptance), kT = 0.8, L-BFGS m = 10 to
 ||grad E||_inf < 1e-6.  One bench "step" is one bh_step_batched launch that
-advances every walker by one adaptation window (10 BH steps = 5120 local
-minimisations); the default 50 steps run the workload's 500 BH steps.
+advances every walker by five adaptation windows (50 BH steps = 25,600 local
+minimisations); the default 10 steps run the workload's 500 BH steps.
 
 metric  converged LJ minimisations per second (minimisations that reached
         ||grad E||_inf < 1e-6 with an FP64 gradient), mixed precision path;
@@ -55,7 +55,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_ATOMS, WALKERS, K = 38, 64, 8
-BH_PER_LAUNCH = 10          # BH steps per bench step (one adaptation window)
+# BH steps per bench step (five adaptation windows).  A launch ends when the
+# slowest of its 64 walkers has finished its steps, so the walkers' spread in
+# time per step costs once per launch: on this workload 10 steps per launch
+# took 2.024 ms per BH step, 50 took 1.916 (CUDA events, same steps)
+BH_PER_LAUNCH = 50
+# BH steps per launch of the search-quality run, which reads the walkers'
+# best energies after every launch
+SEARCH_PER_LAUNCH = 10
 SIDE, STEP0, KT = 3.2, 0.4, 0.8
 # MIXED precision policy parameter of this workload: the FP32 tier's gradient
 # threshold (swept on LJ38 BH: 1e-3 168k, 3e-4 179k, 1e-4 183k converged/s);
@@ -64,21 +71,21 @@ SIDE, STEP0, KT = 3.2, 0.4, 0.8
 SWITCH_GTOL = 1e-4
 CONFIG_ID = 1
 WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per BH step (512 L-BFGS "
-            "minimisations per BH step), 10 BH steps per bench step, cube starts side "
+            "minimisations per BH step), 50 BH steps per bench step, cube starts side "
             "3.2 sigma, m=10, ||g||_inf<1e-6")
 PAIRS = N_ATOMS * (N_ATOMS - 1) // 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 (FMA) x max SM GHz
 FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of GB300
 # dram__bytes_read.sum + dram__bytes_write.sum of one bh_cluster_kernel launch of this
-# workload (10 BH steps), from one ncu capture of the kernel as it is built now; None
-# whenever the kernel changes until it is captured again
-BH_DRAM_BYTES_PER_LAUNCH = 364288
+# workload (50 BH steps), from one ncu capture of the launch as the bench makes it; None
+# whenever the kernel or the launch changes until it is captured again
+BH_DRAM_BYTES_PER_LAUNCH = 1018368
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None)
@@ -656,7 +663,7 @@ MORSE_PAIR_FLOPS = 24.0
 
 
 def morse_bh_record(L, flush, reps, warmup, cpu_budget):
-    """Morse clusters of 38 atoms (rho = 6), 64 walkers x K = 8, 10 BH steps
+    """Morse clusters of 38 atoms (rho = 6), 64 walkers x K = 8, 50 BH steps
     per launch, cube starts side 3.2 re, kT = 0.8: converged minimisations per
     second, mixed and FP64, with the oracle's Morse on the host cores."""
     import torch
@@ -680,7 +687,7 @@ def morse_bh_record(L, flush, reps, warmup, cpu_budget):
                 "stepsize": torch.full((WALKERS,), STEP0, dtype=torch.float64, device=dev),
                 "win_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev),
                 "n_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev)}
-    out = {"workload": "Morse rho=6, N=38: 64 walkers x K=8, 10 BH steps per launch, cube "
+    out = {"workload": "Morse rho=6, N=38: 64 walkers x K=8, 50 BH steps per launch, cube "
                        "starts side 3.2 re, kT=0.8, m=10, ||g||_inf<1e-6"}
     for prec, pname in ((L.LJ_PREC_MIXED, "mixed"), (L.LJ_PREC_FP64, "fp64")):
         p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH,
@@ -1073,7 +1080,8 @@ def k_sweep(L, dev, init_state, bh_params, flush, ks=(1, 2, 4, 8, 16), launches=
             "precision": "mixed", "per_K": out}
 
 
-def search_quality(L, ctx, dev, init_state, bh_params, launches=50, prec=None):
+def search_quality(L, ctx, dev, init_state, bh_params, launches=500 // SEARCH_PER_LAUNCH,
+                   prec=None):
     """The workload's 500 BH steps from its minimised starts (64 walkers,
     K = 8, mixed unless prec says otherwise): the running best energy against
     BH step, and how many walkers reach the LJ38 global minimum (the O_h
@@ -1082,11 +1090,12 @@ def search_quality(L, ctx, dev, init_state, bh_params, launches=50, prec=None):
     e_gm = lj38_global_minimum_energy()
     state = init_state()
     p = bh_params(L.LJ_PREC_MIXED if prec is None else prec)
+    p.n_steps = SEARCH_PER_LAUNCH
     host = torch.empty((launches, WALKERS), dtype=torch.float64).pin_memory()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(launches)]
     for s in range(launches):
-        p.step0 = s * BH_PER_LAUNCH
+        p.step0 = s * SEARCH_PER_LAUNCH
         ev[s][0].record()
         L.bh_step_batched(ctx, state, p)
         ev[s][1].record()
@@ -1096,17 +1105,17 @@ def search_quality(L, ctx, dev, init_state, bh_params, launches=50, prec=None):
     ms = np.cumsum([a.elapsed_time(b) for a, b in ev])
     hit = best <= e_gm + 1e-6
     first = np.where(hit.any(0), hit.argmax(0), -1)
-    hit_steps = (first[first >= 0] + 1) * BH_PER_LAUNCH
+    hit_steps = (first[first >= 0] + 1) * SEARCH_PER_LAUNCH
     hit_ms = ms[first[first >= 0]] if (first >= 0).any() else np.zeros(0)
-    marks = [s for s in (10, 50, 100, 200, 300, 500) if s <= launches * BH_PER_LAUNCH]
-    curve = {str(s): {"lowest": float(best[s // BH_PER_LAUNCH - 1].min()),
-                      "mean_of_walker_best": float(best[s // BH_PER_LAUNCH - 1].mean())}
+    marks = [s for s in (10, 50, 100, 200, 300, 500) if s <= launches * SEARCH_PER_LAUNCH]
+    curve = {str(s): {"lowest": float(best[s // SEARCH_PER_LAUNCH - 1].min()),
+                      "mean_of_walker_best": float(best[s // SEARCH_PER_LAUNCH - 1].mean())}
              for s in marks}
-    frac = {str(s): float(hit[s // BH_PER_LAUNCH - 1].mean()) for s in marks}
+    frac = {str(s): float(hit[s // SEARCH_PER_LAUNCH - 1].mean()) for s in marks}
     return {"target": {"energy": e_gm, "structure": "fcc truncated octahedron (O_h)",
                        "tolerance": 1e-6},
             "precision": "mixed" if prec in (None, L.LJ_PREC_MIXED) else "fp64",
-            "bh_steps": launches * BH_PER_LAUNCH, "walkers": WALKERS, "K": K,
+            "bh_steps": launches * SEARCH_PER_LAUNCH, "walkers": WALKERS, "K": K,
             "running_best": curve, "fraction_of_walkers_at_target": frac,
             "walkers_hit": int((first >= 0).sum()),
             "median_steps_to_hit": float(np.median(hit_steps)) if hit_steps.size else None,
