@@ -361,7 +361,7 @@ def eval_microbench(L, ctx, dev, flush, repeats=100, errors=True):
 def run_reference(args):
     """The FP64 oracle on this host's cores, timed on the headline workload:
     one reference step is one BH step of all 64 walkers (K = 8), a bounded
-    sample of the GPU arm's 10-step bench step."""
+    sample of the GPU arm's bench step of BH_PER_LAUNCH BH steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -388,7 +388,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "fp64",
                        "bh_steps_per_step": 1,
-                       "step": "one BH step of 64 walkers x K=8 (the GPU arm's step is 10)"},
+                       "step": f"one BH step of 64 walkers x K=8 (the GPU arm's step is "
+                               f"{BH_PER_LAUNCH})"},
             "cpu_baseline": {"value": v, "unit": "converged minimisations/s",
                              "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"{args.steps} BH steps x 64 walkers x K=8 = {mins} "
