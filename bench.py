@@ -7,8 +7,9 @@ uniform in a cube of side 3.2 sigma (seeded), minimised once before timing;
 perturbations +-step per coordinate from Philox (initial step 0.4 sigma,
 adapted every 10 steps toward 50% acceptance), kT = 0.8, L-BFGS m = 10 to
 ||grad E||_inf < 1e-6.  One bench "step" is one bh_step_batched launch that
-advances every walker by five adaptation windows (50 BH steps = 25,600 local
-minimisations); the default 10 steps run the workload's 500 BH steps.
+advances every walker by 25 BH steps (12,800 local minimisations); the timed
+steps run the workload's BH steps from step 0 (warm-up launches advance a
+copy of the state), so the default 20 steps are the workload's 500 BH steps.
 
 metric  converged LJ minimisations per second (minimisations that reached
         ||grad E||_inf < 1e-6 with an FP64 gradient), mixed precision path;
@@ -55,11 +56,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_ATOMS, WALKERS, K = 38, 64, 8
-# BH steps per bench step (five adaptation windows).  A launch ends when the
-# slowest of its 64 walkers has finished its steps, so the walkers' spread in
-# time per step costs once per launch: on this workload 10 steps per launch
-# took 2.024 ms per BH step, 50 took 1.916 (CUDA events, same steps)
-BH_PER_LAUNCH = 50
+# BH steps per bench step.  A launch ends when the slowest of its 64 walkers
+# has finished its steps, so the walkers' spread in time per step costs once
+# per launch: on this workload 10 steps per launch took 2.024 ms per BH step,
+# 50 took 1.916 (CUDA events, same steps); 25 makes 20 bench steps the
+# workload's 500 BH steps
+BH_PER_LAUNCH = 25
 # BH steps per launch of the search-quality run, which reads the walkers'
 # best energies after every launch
 SEARCH_PER_LAUNCH = 10
@@ -71,22 +73,22 @@ SIDE, STEP0, KT = 3.2, 0.4, 0.8
 SWITCH_GTOL = 1e-4
 CONFIG_ID = 1
 WORKLOAD = ("LJ38 Basin Hopping: 64 walkers x K=8 candidates per BH step (512 L-BFGS "
-            "minimisations per BH step), 50 BH steps per bench step, cube starts side "
+            "minimisations per BH step), 25 BH steps per bench step, cube starts side "
             "3.2 sigma, m=10, ||g||_inf<1e-6")
 PAIRS = N_ATOMS * (N_ATOMS - 1) // 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e-3   # SMs x FP32 lanes x 2 (FMA) x max SM GHz
 FP64_PEAK_TFLOPS = 1.25                    # nominal FP64 (non-tensor) rate of GB300
 # dram__bytes_read.sum + dram__bytes_write.sum of one bh_cluster_kernel launch of this
-# workload (50 BH steps), from one ncu capture of the launch as the bench makes it; None
+# workload (25 BH steps), from one ncu capture of the launch as the bench makes it; None
 # whenever the kernel or the launch changes until it is captured again
-BH_DRAM_BYTES_PER_LAUNCH = 1018368
+BH_DRAM_BYTES_PER_LAUNCH = 1097216
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
@@ -368,14 +370,16 @@ def run_reference(args):
     x0, seed = start_state(0)
     import oracle as O
     xm, em, st, _, _ = O.lbfgs_batch(x0, WALKERS, uniform_n=N_ATOMS)
-    state = bh_state_np(xm.reshape(WALKERS, -1), em)
+    # warm-up steps advance a copy; the timed steps are the workload's BH
+    # steps 0, 1, ... from the minimised starts, as on the GPU arm
+    wstate = bh_state_np(xm.reshape(WALKERS, -1), em)
     for s in range(args.warmup):
-        O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=s, n_steps=1))
+        O.bh_run(wstate, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=s, n_steps=1))
+    state = bh_state_np(xm.reshape(WALKERS, -1), em)
     conv = mins = 0
     t0 = time.perf_counter()
     for s in range(args.steps):
-        tr = O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=args.warmup + s,
-                                          n_steps=1))
+        tr = O.bh_run(state, O.BhParamsPy(K=K, kT=KT, seed=seed, step0=s, n_steps=1))
         conv += int((tr["trial_status"] == O.CONVERGED).sum())
         mins += tr["trial_status"].size
     dt = time.perf_counter() - t0
@@ -664,7 +668,7 @@ MORSE_PAIR_FLOPS = 24.0
 
 
 def morse_bh_record(L, flush, reps, warmup, cpu_budget):
-    """Morse clusters of 38 atoms (rho = 6), 64 walkers x K = 8, 50 BH steps
+    """Morse clusters of 38 atoms (rho = 6), 64 walkers x K = 8, 25 BH steps
     per launch, cube starts side 3.2 re, kT = 0.8: converged minimisations per
     second, mixed and FP64, with the oracle's Morse on the host cores."""
     import torch
@@ -688,7 +692,7 @@ def morse_bh_record(L, flush, reps, warmup, cpu_budget):
                 "stepsize": torch.full((WALKERS,), STEP0, dtype=torch.float64, device=dev),
                 "win_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev),
                 "n_accept": torch.zeros(WALKERS, dtype=torch.int32, device=dev)}
-    out = {"workload": "Morse rho=6, N=38: 64 walkers x K=8, 50 BH steps per launch, cube "
+    out = {"workload": "Morse rho=6, N=38: 64 walkers x K=8, 25 BH steps per launch, cube "
                        "starts side 3.2 re, kT=0.8, m=10, ||g||_inf<1e-6"}
     for prec, pname in ((L.LJ_PREC_MIXED, "mixed"), (L.LJ_PREC_FP64, "fp64")):
         p = L.BhParams(K=K, kT=KT, seed=seed, n_steps=BH_PER_LAUNCH,
@@ -835,11 +839,14 @@ def run_cuda(args):
         sg_run = 0.0
 
     def timed_run(prec, n_steps, warmup):
-        state = init_state()
+        # warm-up launches advance a copy; the timed launches run the
+        # workload's BH steps 0, 1, ... from the minimised starts
+        wstate = init_state()
         p = bh_params(prec, sg=sg_run)
         for s in range(warmup):
             p.step0 = s * BH_PER_LAUNCH
-            L.bh_step_batched(ctx, state, p)
+            L.bh_step_batched(ctx, wstate, p)
+        state = init_state()
         stats = L.new_stats(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(n_steps)]
@@ -850,7 +857,7 @@ def run_cuda(args):
             t0 = time.perf_counter()
             for s in range(n_steps):
                 flush.fill_(float(s))
-                p.step0 = (warmup + s) * BH_PER_LAUNCH
+                p.step0 = s * BH_PER_LAUNCH
                 ev[s][0].record(stream)
                 L.bh_step_batched(ctx, state, p, None, stats)
                 ev[s][1].record(stream)
@@ -864,9 +871,11 @@ def run_cuda(args):
         """Public API with host buffers, the same steps and L2 flushes as the
         device-timed run: every step copies the walker state from pinned host
         memory to the device, runs the BH launch and copies the updated state
-        back, all between the step's CUDA events."""
+        back, all between the step's CUDA events.  As in timed_run, the timed
+        steps start again from the minimised starts at BH step 0."""
         dstate = init_state()
-        host = {k: v.cpu().pin_memory() for k, v in dstate.items()}
+        host0 = {k: v.cpu() for k, v in dstate.items()}
+        host = {k: v.clone().pin_memory() for k, v in host0.items()}
         p = bh_params(prec, sg=sg_run)
         stats = L.new_stats(dev)
         h2d = sum(v.numel() * v.element_size() for v in host.values())
@@ -874,6 +883,8 @@ def run_cuda(args):
               for _ in range(n_steps)]
         for s in range(warmup + n_steps):
             if s == warmup:
+                for k in host:
+                    host[k].copy_(host0[k])
                 stats.zero_()
                 torch.cuda.synchronize()
                 barrier()
@@ -883,7 +894,7 @@ def run_cuda(args):
                 ev[s - warmup][0].record(stream)
             for k in host:
                 dstate[k].copy_(host[k], non_blocking=True)
-            p.step0 = s * BH_PER_LAUNCH
+            p.step0 = (s if s < warmup else s - warmup) * BH_PER_LAUNCH
             L.bh_step_batched(ctx, dstate, p, None, stats)
             for k in host:
                 host[k].copy_(dstate[k], non_blocking=True)
@@ -989,7 +1000,7 @@ def run_cuda(args):
     if world == 1 and not args.no_extras:
         # ---- errors of the timed workload against the oracle ------------------
         line["errors"] = trial_move_errors(L, ctx, dev, state_end, seed,
-                                           (args.warmup + args.steps) * BH_PER_LAUNCH)
+                                           args.steps * BH_PER_LAUNCH)
         if not args.no_micro:
             line["eval_microbench"] = eval_microbench(L, ctx, dev, flush)
         line["k_sweep"] = k_sweep(L, dev, init_state, bh_params, flush)
