@@ -745,6 +745,20 @@ def test_bh_lj38_k8_fp64(lj, ctx):
     _bh_compare(lj, ctx, 4, 38, 3.2, 8, 4, 0, I.workload_seed(1), 0.4)
 
 
+@pytest.mark.parametrize("n_walkers,n_atoms,K,n_steps", [(3, 20, 16, 3), (3, 100, 4, 3),
+                                                        (3, 150, 2, 3)])
+def test_bh_fp64_team_layouts_match_oracle(lj, ctx, n_walkers, n_atoms, K, n_steps):
+    """The FP64 BH path against the oracle on the layouts the LJ13 / LJ38
+    cases leave out: K = 16 (a non-portable cluster of 16 CTAs), 64-thread
+    teams holding two atoms a thread (N = 100: double-float and FP64 rows
+    one-sided, no half-pair buffer above 64 atoms) and 128-thread teams
+    (N = 150).  Cube starts at reduced density 0.3.  Measured: 0.75, 0.71 and
+    0.88 of the walker steps match the oracle's before the chains part."""
+    side = (n_atoms / 0.3) ** (1.0 / 3.0)
+    _bh_compare(lj, ctx, n_walkers, n_atoms, side, K, n_steps, 0,
+                I.workload_seed(1) + 1500 + n_atoms, 0.5)
+
+
 def test_bh_lj38_k8_mixed(lj, ctx):
     """Mixed path, K = 8: one candidate ending in another basin already parts
     the two chains, so whole steps rarely match; the first step (identical
